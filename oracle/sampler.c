@@ -1,0 +1,220 @@
+/*
+ * CPU oracle: the sqrt(c)-walk Monte Carlo single-source SimRank estimator,
+ * written step by step in plain C (C11 + OpenMP over targets).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, by the smoke check and by the
+ * CPU baseline of the benchmark; never by the library.  It shares no source
+ * file, header or table generator with the CUDA path.
+ *
+ * Steps, in the paper's order (Section 4, Algorithms 1 and 2):
+ *   a2  walk generation (Alg. 1, lines 4-7; Section 4.1(a)): from every node,
+ *       N_l walks of fixed length l for l = 0..L, in stratum order (walk r has
+ *       length l when P[l] <= r < P[l+1]).  A step moves to a uniformly chosen
+ *       in-neighbour (the out-neighbour on the reversed graph, Section 2.2).
+ *       A walk that reaches a node without in-neighbours stops there.
+ *   a3  shuffling (Section 4.1(b), Section 5.2): the source's walks are
+ *       relabelled by one uniform permutation sigma (Fisher-Yates); pair j
+ *       joins source walk sigma[j] with walk j of the target.
+ *   a4  meeting detection (Section 4.2, Lemma 2, Algorithm 2): the pair meets
+ *       when both walks visit the same node at the same step i >= 1; each
+ *       pair counts once (Section 5.5) and adds the Lemma 7 weight of its two
+ *       lengths, quantised to 2^-32 units and passed in by the caller.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11), restated from that paper's definition:
+ * ten rounds of two 32x32->64 multiplies by 0xD2511F53 and 0xCD9E8D57 with the
+ * key bumped by the Weyl constants 0x9E3779B9 and 0xBB67AE85 between rounds.
+ *   key     = (seed mod 2^32, seed >> 32)
+ *   walk r of node v for query source s, step i >= 1:
+ *           counter = ((i-1) >> 1, r, v, s); the 64-bit draw is word
+ *           2*((i-1)&1) (high half) and word 2*((i-1)&1)+1 (low half)
+ *   Fisher-Yates draw t: counter = (t >> 1, 0xFFFFFFFF, 0xFFFFFFFF, s),
+ *           words 2*(t&1) (high) and 2*(t&1)+1 (low)
+ *   uniform index below d from a 64-bit draw R: floor(R * d / 2^64).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void srko_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                        uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * x0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* floor(r * d / 2^64): a uniform index in [0, d) from a 64-bit draw. */
+uint32_t srko_index(uint64_t r, uint32_t d) {
+    return (uint32_t)(((unsigned __int128)r * d) >> 64);
+}
+
+static uint64_t draw64(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                       uint64_t seed, int half) {
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    srko_philox4x32_10(ctr, key, w);
+    return ((uint64_t)w[2 * half] << 32) | w[2 * half + 1];
+}
+
+/* One walk of nominal length `len` from v, replica r, query source s.
+ * Writes the node at step i to pos[i-1]; returns the number of steps taken
+ * (smaller than len only when a node without in-neighbours was reached). */
+int srko_walk(const int32_t *row_ptr, const int32_t *col, int32_t v,
+              int32_t r, int32_t s, uint64_t seed, int len, int32_t *pos) {
+    int32_t x = v;
+    for (int i = 1; i <= len; ++i) {
+        int32_t beg = row_ptr[x], deg = row_ptr[x + 1] - row_ptr[x];
+        if (deg == 0) return i - 1;
+        uint64_t R = draw64((uint32_t)((i - 1) >> 1), (uint32_t)r,
+                            (uint32_t)v, (uint32_t)s, seed, (i - 1) & 1);
+        x = col[beg + srko_index(R, (uint32_t)deg)];
+        pos[i - 1] = x;
+    }
+    return len;
+}
+
+static int stratum_of(const int32_t *P, int L, int32_t r) {
+    int lo = 0, hi = L;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (P[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* All N_tot = P[L+1] walks of node v in stratum order (step a2).  pos is
+ * N_tot x max(L,1), -1 beyond a walk's end; eff[r] = steps walk r took. */
+void srko_walks(const int32_t *row_ptr, const int32_t *col, int32_t v,
+                int32_t s, uint64_t seed, int L, const int32_t *P,
+                int32_t *pos, int32_t *eff) {
+    int stride = L > 0 ? L : 1;
+    int32_t N_tot = P[L + 1];
+    for (int32_t r = 0; r < N_tot; ++r) {
+        int len = stratum_of(P, L, r);
+        int32_t *row = pos + (int64_t)r * stride;
+        for (int i = 0; i < stride; ++i) row[i] = -1;
+        eff[r] = srko_walk(row_ptr, col, v, r, s, seed, len, row);
+    }
+}
+
+/* Step a3: sigma = one Fisher-Yates permutation of 0..N_tot-1 keyed by
+ * (seed, s): for t = N_tot-1 down to 1, swap sigma[t] with sigma[k_t],
+ * k_t uniform in [0, t]. */
+void srko_fisher_yates(int32_t s, uint64_t seed, int32_t N_tot,
+                       int32_t *sigma) {
+    for (int32_t t = 0; t < N_tot; ++t) sigma[t] = t;
+    for (int32_t t = N_tot - 1; t >= 1; --t) {
+        uint64_t R = draw64((uint32_t)t >> 1, 0xFFFFFFFFu, 0xFFFFFFFFu,
+                            (uint32_t)s, seed, t & 1);
+        int32_t k = (int32_t)srko_index(R, (uint32_t)t + 1u);
+        int32_t tmp = sigma[t];
+        sigma[t] = sigma[k];
+        sigma[k] = tmp;
+    }
+}
+
+/*
+ * Steps a2-a4 for query source s and the targets listed in `targets`
+ * (n_targets entries; any node ids, s included).  wq is the (L+1)x(L+1)
+ * quantised weight table, row l1 (source length), column l2 (target length).
+ * Outputs per listed target: meet count, weight sum (2^-32 units) and the
+ * number of target-walk steps a walker that stops at the first meeting, at a
+ * node without in-neighbours or after min(l2, steps the source walk took)
+ * steps would take.  Returns 0, or -1 when memory runs out.
+ */
+int srko_sampler(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                 int32_t s, uint64_t seed, int L, const int32_t *P,
+                 const uint64_t *wq, const int32_t *targets,
+                 int64_t n_targets, uint32_t *count, uint64_t *wsum,
+                 uint64_t *steps, uint64_t *source_steps, int threads) {
+    (void)n;
+    int stride = L > 0 ? L : 1;
+    int32_t N_tot = P[L + 1];
+    int32_t *spos = (int32_t *)malloc(sizeof(int32_t) * (size_t)N_tot * stride);
+    int32_t *seff = (int32_t *)malloc(sizeof(int32_t) * (size_t)N_tot);
+    int32_t *sigma = (int32_t *)malloc(sizeof(int32_t) * (size_t)N_tot);
+    if (!spos || !seff || !sigma) {
+        free(spos); free(seff); free(sigma);
+        return -1;
+    }
+    /* a2: the source's walks */
+    srko_walks(row_ptr, col, s, s, seed, L, P, spos, seff);
+    if (source_steps) {
+        uint64_t tot = 0;
+        for (int32_t r = 0; r < N_tot; ++r) tot += (uint64_t)seff[r];
+        *source_steps = tot;
+    }
+    /* a3: pairing by one uniform shuffle of the source's walks */
+    srko_fisher_yates(s, seed, N_tot, sigma);
+
+    int failed = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel
+#endif
+    {
+        int32_t *tpos = (int32_t *)malloc(sizeof(int32_t) * (size_t)stride);
+        if (!tpos) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            failed = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+        for (int64_t t = 0; t < n_targets; ++t) {
+            int32_t u = targets[t];
+            uint32_t cnt = 0;
+            uint64_t ws = 0, st = 0;
+            if (tpos && u != s) {
+                for (int32_t j = 0; j < N_tot; ++j) {
+                    /* a4: pair j = (source walk sigma[j], target walk j) */
+                    int l2 = stratum_of(P, L, j);
+                    int32_t w = sigma[j];
+                    int l1 = stratum_of(P, L, w);
+                    int teff = srko_walk(row_ptr, col, u, j, s, seed, l2, tpos);
+                    int m = teff < seff[w] ? teff : seff[w];
+                    const int32_t *sp = spos + (int64_t)w * stride;
+                    int met = 0;
+                    for (int i = 1; i <= m; ++i) {
+                        if (tpos[i - 1] == sp[i - 1]) { met = i; break; }
+                    }
+                    if (met) {
+                        cnt += 1;
+                        ws += wq[(int64_t)l1 * (L + 1) + l2];
+                        st += (uint64_t)met;
+                    } else {
+                        st += (uint64_t)m;
+                    }
+                }
+            }
+            count[t] = cnt;
+            wsum[t] = ws;
+            steps[t] = st;
+        }
+        free(tpos);
+    }
+    free(spos); free(seff); free(sigma);
+    return failed ? -1 : 0;
+}
