@@ -1,0 +1,173 @@
+/*
+ * srk.h -- C ABI of the GB300 single-source SimRank library.
+ *
+ * The library computes the sqrt(c)-walk Monte Carlo estimate of single-source
+ * SimRank described in "Massively Parallel Single-Source SimRanks in o(log n)
+ * Rounds" (Luo and Zhu, arXiv 2304.04015), on one CUDA device (sm_103a).
+ * The paper's MPC rounds become kernel phases on one stream:
+ *   a1  sample-count table (Algorithm 1 lines 3-5, Algorithm 2 line 2, Lemma 7)
+ *   a2  source walks of fixed lengths (Algorithm 1 lines 4-7, Section 4.1(a))
+ *   a3  one uniform shuffle of the source's walks (Section 4.1(b), 5.2)
+ *   a4  target walks, meeting detection and weighted counting (Section 4.2,
+ *       Lemma 2, Lemma 3, Algorithm 2, Section 5.5)
+ *   a5  scores s~(s,u) = sum of weights / z (Algorithm 2 line 10)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Graph: an in-neighbour CSR.  row_ptr has n+1 int32 entries, row_ptr[0] = 0,
+ *   row_ptr[n] = m, non-decreasing; col has m int32 entries in [0, n), and
+ *   col[row_ptr[v] .. row_ptr[v+1]) lists I(v), the in-neighbours of v
+ *   (Eq. 1).  A walk moves from v to a uniform member of I(v), i.e. along a
+ *   reversed edge (the graph G-bar of Lemma 2).  The list order matters only
+ *   for reproducibility: the k-th entry is chosen by index.
+ * Random numbers: Philox4x32-10 keyed by (seed mod 2^32, seed >> 32); the
+ *   counter of walk r of node v for query source s at step i >= 1 is
+ *   ((i-1) >> 1, r, v, s), so every walk is reproducible on its own.
+ * Errors: every function returns SRK_OK (0) or a negative code; the message
+ *   of the last failure on the calling thread is srk_last_error().  On error
+ *   no output is guaranteed to be written.
+ * Pointers: unless a flag says otherwise, an output pointer may be host or
+ *   device memory (the library asks CUDA which).  With host output pointers
+ *   the call copies results back and synchronises the stream before it
+ *   returns; with device pointers it only enqueues work on `cuda_stream`
+ *   (a cudaStream_t; NULL = the legacy default stream).
+ * Determinism: identical graph, source, c, eps, seed and options give
+ *   bit-identical counts, weight sums and scores, whatever the launch shape.
+ * Threads: queries only read the graph, so concurrent queries on different
+ *   streams are safe.  Each call allocates its scratch from a library-owned
+ *   stream-ordered pool on the stream it runs on.
+ */
+#ifndef SRK_H
+#define SRK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define SRK_OK        0
+#define SRK_EINVAL   (-1)  /* an argument is out of range or malformed */
+#define SRK_ENOMEM   (-2)  /* a device or host allocation failed */
+#define SRK_ECUDA    (-3)  /* a CUDA runtime call or a kernel launch failed */
+#define SRK_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define SRK_ENOTSUP  (-5)  /* the request is valid but not supported */
+
+/* srk_graph_load flags. */
+#define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */
+#define SRK_VALIDATE    2  /* accepted; the CSR invariants are always checked */
+
+/* Upper bounds of this build. */
+#define SRK_MAX_LEN   255          /* largest truncation length L */
+#define SRK_MAX_WALKS (1 << 24)    /* largest N_tot, walks per node */
+
+typedef struct srk_graph srk_graph;
+typedef struct srk_linear_ctx srk_linear_ctx;
+
+/* Per-query statistics (host memory), filled when srk_opts.stats != NULL. */
+typedef struct srk_stats {
+    double  z;              /* expected number of walk samples (Alg. 2 line 2) */
+    int32_t L;              /* truncation length */
+    int32_t n_walks;        /* N_tot = sum_l N_l, walks per node and pairs per target */
+    int32_t n_active_pairs; /* pairs whose both walks take >= 1 step */
+    int32_t reserved;
+    uint64_t source_steps;  /* steps taken by the source's walks */
+    uint64_t target_steps;  /* target-walk steps taken over all targets */
+} srk_stats;
+
+/* Query options; pass NULL for the paper's defaults. */
+typedef struct srk_opts {
+    double   z_override;   /* > 0: use as z instead of ln(2n^q)/(2(eps-3/n^p)^2);
+                              eps is then not used */
+    int32_t  L_override;   /* >= 0: truncation length instead of
+                              floor(p ln n / ln(1/sqrt(c))); < 0: paper */
+    int32_t  flags;        /* reserved, 0 */
+    double   p;            /* threshold knob of Appendix B.5, >= 1 (0 means 1) */
+    double   q;            /* failure knob of Appendix B.5, >= 1 (0 means 1) */
+    uint32_t *step_counts; /* NULL or n entries (host or device memory):
+                              target-walk steps taken per target */
+    srk_stats *stats;      /* NULL or host pointer; forces a stream sync */
+    void     *timing_events; /* NULL or a host array of two cudaEvent_t: [0] is
+                              recorded on the query's stream just before the
+                              target-walk kernel (step a4), [1] just after */
+} srk_opts;
+
+/*
+ * srk_graph_load -- make a graph resident on the current CUDA device.
+ *   row_ptr, col : the in-neighbour CSR described above (n+1 and m entries).
+ *   n            : number of nodes, 1 <= n < 2^31.
+ *   m            : number of edges, 0 <= m < 2^31 (int32 offsets).
+ *   flags        : SRK_DEVICE_PTRS: the arrays live on the current device and
+ *                  are borrowed; the caller keeps them alive and unchanged
+ *                  until srk_graph_free.  Otherwise they are host arrays and
+ *                  are copied.  SRK_VALIDATE is accepted and implied.
+ * The CSR invariants (row_ptr[0] = 0, row_ptr[n] = m, row_ptr non-decreasing,
+ * 0 <= col < n) are always checked on the device before the handle is
+ * returned; a violation returns SRK_EINVAL.  The walk kernels rely on them.
+ *   edge_w       : NULL, or m FP32 edge weights aligned with col (used by the
+ *                  linearised form); copied unless SRK_DEVICE_PTRS.
+ *   out          : receives the handle.
+ * Storage follows the paper's reversed graph G-bar (Algorithm 1 lines 1-2):
+ * walks read in-neighbour lists.  The call is synchronous.
+ */
+int srk_graph_load(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                   int64_t m, int flags, const float *edge_w, srk_graph **out);
+
+/* srk_graph_free -- release a handle and the device memory it owns.
+ * Waits for the device; NULL is accepted. */
+int srk_graph_free(srk_graph *g);
+
+/* srk_graph_info -- n and m of a loaded graph (either pointer may be NULL). */
+int srk_graph_info(const srk_graph *g, int32_t *n, int64_t *m);
+
+/*
+ * srk_single_source -- estimate s~(s, u) for every node u (Algorithms 1, 2).
+ *   s     : query source, 0 <= s < n.
+ *   c     : SimRank decay factor, 0 < c < 1 (walks continue w.p. sqrt(c)).
+ *   eps   : absolute error target, 3/n^p < eps < 1 (Theorem 6); z =
+ *           ln(2n^q) / (2 (eps - 3/n^p)^2) walk samples per node.
+ *   seed  : 64-bit Philox key.
+ *   opt   : NULL or options (see srk_opts).
+ *   scores      : n FP64 outputs, s~(s, u) = W_u 2^-32 / z, s~(s, s) = 1, and
+ *                 0 for a node without in-neighbours.
+ *   meet_counts : NULL or n uint32 outputs, meeting walk pairs per target.
+ *   weight_sums : NULL or n uint64 outputs, W_u = sum over meeting pairs of
+ *                 round(a(l1) a(l2) 2^32), a(l) = |Z_l| / |Z^_l| (Lemma 7).
+ *   cuda_stream : stream to run on (see Pointers).
+ * Walk lengths: N_l = ceil(z sqrt(c)^l (1 - sqrt(c))) walks of length l for
+ * l = 0..L, L = floor(p ln n / ln(1/sqrt c)).  The source's N_tot walks are
+ * shuffled by one Fisher-Yates permutation; pair j joins source walk sigma(j)
+ * with target walk j.  A pair meets when both walks are at the same node at
+ * the same step i >= 1; it counts once.  A walk stops early at a node without
+ * in-neighbours.  Returns SRK_EINVAL for s, c, eps, p, q out of range, or
+ * when L > SRK_MAX_LEN or N_tot > SRK_MAX_WALKS.
+ */
+int srk_single_source(const srk_graph *g, int32_t s, double c, double eps,
+                      uint64_t seed, const srk_opts *opt, double *scores,
+                      uint32_t *meet_counts, uint64_t *weight_sums,
+                      void *cuda_stream);
+
+/*
+ * srk_multi_source -- k independent single-source queries.
+ *   sources : k source nodes (host memory).
+ *   eps     : k error targets (host memory), one per source.
+ *   scores  : k x n FP64 outputs, row i for sources[i].
+ *   meet_counts : NULL or k x n uint32 outputs.
+ * Query i uses the same seed; its walks differ because the source is part of
+ * every Philox counter.  Results equal k calls of srk_single_source.
+ * opt->step_counts must be NULL here; opt->stats, if set, receives totals.
+ */
+int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
+                     double c, const double *eps, uint64_t seed,
+                     const srk_opts *opt, double *scores,
+                     uint32_t *meet_counts, void *cuda_stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *srk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRK_H */

@@ -1,0 +1,249 @@
+"""Python binding of the GB300 single-source SimRank library (``libsrk.so``).
+
+A thin ctypes layer over the C ABI declared in ``include/srk.h``: it only
+marshals arguments (array pointers, sizes, the CUDA stream) and turns negative
+return codes into ``SrkError``.  Every step of a query runs in the library's
+CUDA kernels; there is no CPU fallback.  Importing this package loads
+``libsrk.so`` and fails loudly (``ImportError``) when it has not been built
+(``python -m paper_2304_04015_gb300.build``).
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays.  Device tensors are
+passed as device pointers; host arrays as host pointers (the library then
+copies results back and synchronises the stream before returning).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "SrkError", "SrkOpts", "SrkStats", "Graph",
+    "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
+    "srk_multi_source", "srk_last_error", "library_path",
+    "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
+    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_MAX_LEN",
+    "SRK_MAX_WALKS",
+]
+
+SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
+SRK_DEVICE_PTRS, SRK_VALIDATE = 1, 2
+SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libsrk.so")
+
+if not os.path.exists(library_path):
+    raise ImportError(
+        "libsrk.so is not built; run `python -m paper_2304_04015_gb300.build` "
+        "(needs nvcc).  There is no CPU fallback.")
+_lib = ctypes.CDLL(library_path)
+
+
+class SrkError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("srk error %d: %s" % (code, message))
+        self.code = code
+
+
+class SrkStats(ctypes.Structure):
+    _fields_ = [("z", ctypes.c_double), ("L", ctypes.c_int32),
+                ("n_walks", ctypes.c_int32), ("n_active_pairs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("source_steps", ctypes.c_uint64),
+                ("target_steps", ctypes.c_uint64)]
+
+
+class SrkOpts(ctypes.Structure):
+    _fields_ = [("z_override", ctypes.c_double), ("L_override", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("p", ctypes.c_double),
+                ("q", ctypes.c_double), ("step_counts", ctypes.c_void_p),
+                ("stats", ctypes.POINTER(SrkStats)), ("timing_events", ctypes.c_void_p)]
+
+
+_vp = ctypes.c_void_p
+_lib.srk_graph_load.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int64,
+                                ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_lib.srk_graph_free.argtypes = [_vp]
+_lib.srk_graph_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int64)]
+_lib.srk_single_source.argtypes = [_vp, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_uint64,
+                                   ctypes.POINTER(SrkOpts), _vp, _vp, _vp, _vp]
+_lib.srk_multi_source.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double,
+                                  _vp, ctypes.c_uint64, ctypes.POINTER(SrkOpts),
+                                  _vp, _vp, _vp]
+_lib.srk_last_error.restype = ctypes.c_char_p
+for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
+           "srk_single_source", "srk_multi_source"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def srk_last_error() -> str:
+    return (_lib.srk_last_error() or b"").decode(errors="replace")
+
+
+def _check(rc: int) -> None:
+    if rc != SRK_OK:
+        raise SrkError(rc, srk_last_error())
+
+
+# unsigned outputs may also be given as signed tensors of the same width
+_SAME_WIDTH = {"uint32": ("uint32", "int32"), "uint64": ("uint64", "int64")}
+
+
+def _ptr(a, dtype=None):
+    """(pointer, is_device, keepalive) of a torch tensor or numpy array."""
+    if a is None:
+        return None, False, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if dtype is not None and str(a.dtype)[6:] not in _SAME_WIDTH.get(dtype, (dtype,)):
+                raise TypeError("expected a %s tensor, got %s" % (dtype, a.dtype))
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return a.data_ptr(), a.is_cuda, a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.asarray(a)
+    if dtype is not None and arr.dtype != np.dtype(dtype):
+        raise TypeError("expected a %s array, got %s" % (dtype, arr.dtype))
+    if not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return arr.ctypes.data, False, arr
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """Handle of a resident graph (``srk_graph*``); frees itself when closed."""
+
+    def __init__(self, handle: int, n: int, m: int, keep):
+        self.handle = handle
+        self.n = n
+        self.m = m
+        self._keep = keep
+
+    def close(self) -> None:
+        if self.handle:
+            h, self.handle = self.handle, 0
+            _check(_lib.srk_graph_free(h))
+            self._keep = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srk_graph_load(row_ptr, col, n: Optional[int] = None, m: Optional[int] = None,
+                   flags: Optional[int] = None, edge_w=None) -> Graph:
+    """Load an in-neighbour CSR (see ``include/srk.h``).  Device tensors are
+    borrowed (SRK_DEVICE_PTRS); host arrays are copied to the current device."""
+    rp, rp_dev, k1 = _ptr(row_ptr, "int32")
+    cl, cl_dev, k2 = _ptr(col, "int32")
+    ew, ew_dev, k3 = _ptr(edge_w, "float32")
+    if n is None:
+        n = (row_ptr.numel() if hasattr(row_ptr, "numel") else np.asarray(row_ptr).size) - 1
+    if m is None:
+        m = col.numel() if hasattr(col, "numel") else np.asarray(col).size
+    if flags is None:
+        flags = SRK_DEVICE_PTRS if rp_dev else 0
+    if rp_dev != cl_dev or (edge_w is not None and ew_dev != rp_dev):
+        raise ValueError("row_ptr, col and edge_w must all be on the device or all on the host")
+    h = _vp()
+    _check(_lib.srk_graph_load(rp, cl, int(n), int(m), int(flags), ew, ctypes.byref(h)))
+    keep = (k1, k2, k3) if flags & SRK_DEVICE_PTRS else None
+    return Graph(h.value, int(n), int(m), keep)
+
+
+def srk_graph_free(g: Graph) -> None:
+    g.close()
+
+
+def srk_graph_info(g: Graph):
+    n = ctypes.c_int32()
+    m = ctypes.c_int64()
+    _check(_lib.srk_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def _opts(z_override=None, L_override=None, p=None, q=None, step_counts=None,
+          stats: Optional[SrkStats] = None, timing_events=None):
+    o = SrkOpts()
+    o.z_override = float(z_override) if z_override else 0.0
+    o.L_override = int(L_override) if L_override is not None else -1
+    o.flags = 0
+    o.p = float(p) if p else 0.0
+    o.q = float(q) if q else 0.0
+    sp, _, keep = _ptr(step_counts, "uint32")
+    o.step_counts = sp
+    o.stats = ctypes.pointer(stats) if stats is not None else None
+    ev_keep = None
+    if timing_events is not None:
+        # two torch.cuda.Event objects (or raw cudaEvent_t handles)
+        handles = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in timing_events]
+        ev_keep = (ctypes.c_void_p * 2)(*handles)
+        o.timing_events = ctypes.cast(ev_keep, ctypes.c_void_p).value
+    return o, (keep, ev_keep)
+
+
+def srk_single_source(g: Graph, s: int, c: float, eps: float, seed: int,
+                      scores, meet_counts=None, weight_sums=None, *,
+                      z_override=None, L_override=None, p=None, q=None,
+                      step_counts=None, stats: Optional[SrkStats] = None,
+                      timing_events=None, stream=None) -> None:
+    """One query (``srk_single_source``): fills ``scores`` (n float64) and,
+    when given, ``meet_counts`` (n uint32), ``weight_sums`` (n uint64),
+    ``step_counts`` (n uint32) and ``stats``.  ``timing_events``: two
+    ``torch.cuda.Event(enable_timing=True)`` recorded around the target-walk
+    kernel on the query's stream."""
+    sc, _, k1 = _ptr(scores, "float64")
+    mc, _, k2 = _ptr(meet_counts, "uint32")
+    ws, _, k3 = _ptr(weight_sums, "uint64")
+    o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events)
+    rc = _lib.srk_single_source(g.handle, int(s), float(c), float(eps),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
+                                sc, mc, ws, _stream_handle(stream))
+    del k1, k2, k3, k4
+    _check(rc)
+
+
+def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
+                     meet_counts=None, *, z_override=None, L_override=None,
+                     p=None, q=None, stats: Optional[SrkStats] = None,
+                     stream=None) -> None:
+    """k queries (``srk_multi_source``): ``sources`` and ``eps`` are host
+    sequences of length k; ``scores`` is k x n float64."""
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    k = src.size
+    eps_a = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (k,)))
+    sc, _, k1 = _ptr(scores, "float64")
+    mc, _, k2 = _ptr(meet_counts, "uint32")
+    o, _ = _opts(z_override, L_override, p, q, None, stats)
+    rc = _lib.srk_multi_source(g.handle, src.ctypes.data, k, float(c), eps_a.ctypes.data,
+                               int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), sc, mc,
+                               _stream_handle(stream))
+    del k1, k2
+    _check(rc)

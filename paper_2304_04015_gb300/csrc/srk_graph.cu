@@ -1,0 +1,269 @@
+// Graph residency, error reporting, memory pools and the sample-count table.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "srk_internal.h"
+
+namespace srk {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? SRK_ENOMEM : SRK_ECUDA;
+  return fail(code, "%s: %s (%s)", what, cudaGetErrorString(e),
+              cudaGetErrorName(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+static int g_sms[64] = {};
+
+cudaMemPool_t pool(int device) {
+  if (device < 0 || device >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[device]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    // keep freed blocks cached for the next query
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[device] = p;
+  }
+  return g_pools[device];
+}
+
+int sm_count(int device) {
+  if (device < 0 || device >= 64) return 1;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_sms[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) !=
+            cudaSuccess || v <= 0)
+      v = 1;
+    g_sms[device] = v;
+  }
+  return g_sms[device];
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Algorithm 1 line 3 (truncation), line 5 (N_i), Algorithm 2 line 2 (z, Z, Z^),
+// Lemma 7 (a(l) = |Z_l| / |Z^_l|), Appendix B.5 (p, q).  FP64, evaluated in a
+// fixed order (host code is built without floating-point contraction):
+//   z   = ln(2 n^q) / (2 lambda^2),  lambda = eps - 3 / n^p
+//   L   = floor(p ln n / (-ln sqrt(c)))
+//   Z_l = z * (sqrt(c)^l * (1 - sqrt(c))),  N_l = ceil(Z_l),  a(l) = Z_l / N_l
+int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
+                const srk_opts *opt, QueryTab *t) {
+  if (n < 1) return fail(SRK_EINVAL, "graph has no nodes");
+  if (s < 0 || s >= n) return fail(SRK_EINVAL, "source %d outside [0, %d)", s, n);
+  if (!(c > 0.0 && c < 1.0)) return fail(SRK_EINVAL, "c = %g outside (0, 1)", c);
+  double p = 1.0, q = 1.0, z_ovr = 0.0;
+  int32_t L_ovr = -1;
+  if (opt) {
+    if (opt->p != 0.0) p = opt->p;
+    if (opt->q != 0.0) q = opt->q;
+    z_ovr = opt->z_override;
+    L_ovr = opt->L_override;
+  }
+  if (!(p >= 1.0) || !(q >= 1.0) || !isfinite(p) || !isfinite(q))
+    return fail(SRK_EINVAL, "p = %g and q = %g must be >= 1", p, q);
+  const double rc = sqrt(c);
+  double z;
+  if (z_ovr > 0.0) {
+    if (!isfinite(z_ovr)) return fail(SRK_EINVAL, "z_override is not finite");
+    z = z_ovr;
+  } else {
+    const double thr = 3.0 / pow((double)n, p);
+    if (!(eps > thr && eps < 1.0))
+      return fail(SRK_EINVAL, "eps = %g must satisfy 3/n^p = %g < eps < 1", eps, thr);
+    const double lam = eps - thr;
+    z = log(2.0 * pow((double)n, q)) / (2.0 * lam * lam);
+  }
+  int L;
+  if (L_ovr >= 0) {
+    L = L_ovr;
+  } else {
+    const double Lf = floor(p * log((double)n) / (-log(rc)));
+    if (!(Lf <= (double)SRK_MAX_LEN))
+      return fail(SRK_EINVAL, "truncation length %g exceeds %d", Lf, SRK_MAX_LEN);
+    L = (int)Lf;
+  }
+  if (L > SRK_MAX_LEN)
+    return fail(SRK_EINVAL, "truncation length %d exceeds %d", L, SRK_MAX_LEN);
+  t->s = s;
+  t->n = n;
+  t->L = L;
+  t->key0 = (uint32_t)seed;
+  t->key1 = (uint32_t)(seed >> 32);
+  t->z = z;
+  int64_t acc = 0;
+  t->P[0] = 0;
+  for (int l = 0; l <= L; ++l) {
+    const double Zl = z * (pow(rc, (double)l) * (1.0 - rc));
+    const double Nl = ceil(Zl);
+    if (!(Nl >= 1.0) || Nl > (double)SRK_MAX_WALKS)
+      return fail(SRK_EINVAL, "walk count %g for length %d out of range", Nl, l);
+    acc += (int64_t)Nl;
+    if (acc > SRK_MAX_WALKS)
+      return fail(SRK_EINVAL, "N_tot exceeds %d walks", SRK_MAX_WALKS);
+    t->a[l] = Zl / Nl;
+    t->P[l + 1] = (int32_t)acc;
+  }
+  t->N_tot = (int32_t)acc;
+  return SRK_OK;
+}
+
+// Checks row_ptr[0] = 0, row_ptr[n] = m, row_ptr non-decreasing and
+// 0 <= col < n; sets *bad to 1 on any violation.
+__global__ void k_validate_csr(const int32_t *__restrict__ row_ptr,
+                               const int32_t *__restrict__ col, int32_t n,
+                               int64_t m, int *bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0 && (row_ptr[0] != 0 || (int64_t)row_ptr[n] != m)) *bad = 1;
+  for (int64_t v = t0; v < n; v += stride)
+    if (row_ptr[v + 1] < row_ptr[v]) *bad = 1;
+  for (int64_t e = t0; e < m; e += stride) {
+    const int32_t x = col[e];
+    if (x < 0 || x >= n) *bad = 1;
+  }
+}
+
+}  // namespace srk
+
+using namespace srk;
+
+extern "C" const char *srk_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int srk_graph_info(const srk_graph *g, int32_t *n, int64_t *m) {
+  if (!g) return fail(SRK_EINVAL, "null graph");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  return SRK_OK;
+}
+
+extern "C" int srk_graph_free(srk_graph *g) {
+  if (!g) return SRK_OK;
+  int rc = SRK_OK;
+  {
+    DeviceGuard guard(g->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_fail(e, "srk_graph_free: synchronize");
+    if (g->own_row_ptr) cudaFree(g->own_row_ptr);
+    if (g->own_col) cudaFree(g->own_col);
+    if (g->own_w) cudaFree(g->own_w);
+  }
+  delete g;
+  return rc;
+}
+
+extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
+                              int32_t n, int64_t m, int flags,
+                              const float *edge_w, srk_graph **out) {
+  clear_error();
+  if (!out) return fail(SRK_EINVAL, "out is null");
+  *out = nullptr;
+  if (n < 1) return fail(SRK_EINVAL, "n = %d must be >= 1", n);
+  if (m < 0 || m > INT32_MAX) return fail(SRK_EINVAL, "m = %lld outside [0, 2^31)", (long long)m);
+  if (!row_ptr || (m > 0 && !col)) return fail(SRK_EINVAL, "null CSR array");
+  if (flags & ~(SRK_DEVICE_PTRS | SRK_VALIDATE))
+    return fail(SRK_EINVAL, "unknown flags 0x%x", flags);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "srk_graph_load: no CUDA device");
+  srk_graph *g = new srk_graph;
+  g->n = n;
+  g->m = m;
+  g->device = dev;
+  if (flags & SRK_DEVICE_PTRS) {
+    if (!is_device_ptr(row_ptr) || (m > 0 && !is_device_ptr(col)) ||
+        (edge_w && m > 0 && !is_device_ptr(edge_w))) {
+      delete g;
+      return fail(SRK_EINVAL, "SRK_DEVICE_PTRS given but an array is not device memory");
+    }
+    g->row_ptr = row_ptr;
+    g->col = col;
+    g->edge_w = edge_w;
+  } else {
+    const size_t rb = sizeof(int32_t) * ((size_t)n + 1);
+    const size_t cb = sizeof(int32_t) * (size_t)(m > 0 ? m : 1);
+    if ((e = cudaMalloc(&g->own_row_ptr, rb)) != cudaSuccess ||
+        (e = cudaMalloc(&g->own_col, cb)) != cudaSuccess ||
+        (edge_w && (e = cudaMalloc(&g->own_w, sizeof(float) * (size_t)(m > 0 ? m : 1))) != cudaSuccess)) {
+      int rc = cuda_fail(e, "srk_graph_load: device allocation");
+      srk_graph_free(g);
+      return rc;
+    }
+    if ((e = cudaMemcpy(g->own_row_ptr, row_ptr, rb, cudaMemcpyDefault)) != cudaSuccess ||
+        (m > 0 && (e = cudaMemcpy(g->own_col, col, sizeof(int32_t) * (size_t)m,
+                                  cudaMemcpyDefault)) != cudaSuccess) ||
+        (edge_w && m > 0 && (e = cudaMemcpy(g->own_w, edge_w, sizeof(float) * (size_t)m,
+                                            cudaMemcpyDefault)) != cudaSuccess)) {
+      int rc = cuda_fail(e, "srk_graph_load: copy to device");
+      srk_graph_free(g);
+      return rc;
+    }
+    g->row_ptr = g->own_row_ptr;
+    g->col = g->own_col;
+    g->edge_w = g->own_w;
+  }
+  {  // always validate: the walk kernels index with these values
+    int *bad = nullptr;
+    int hbad = 0;
+    if ((e = cudaMalloc(&bad, sizeof(int))) != cudaSuccess) {
+      int rc = cuda_fail(e, "srk_graph_load: validation flag");
+      srk_graph_free(g);
+      return rc;
+    }
+    cudaMemset(bad, 0, sizeof(int));
+    const int blocks = sm_count(dev) * 4;
+    k_validate_csr<<<blocks, 256>>>(g->row_ptr, g->col, n, m, bad);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(bad);
+    if (e != cudaSuccess) {
+      int rc = cuda_fail(e, "srk_graph_load: validation");
+      srk_graph_free(g);
+      return rc;
+    }
+    if (hbad) {
+      srk_graph_free(g);
+      return fail(SRK_EINVAL, "malformed CSR: row_ptr must start at 0, end at m and "
+                              "not decrease; col entries must lie in [0, n)");
+    }
+  }
+  *out = g;
+  return SRK_OK;
+}

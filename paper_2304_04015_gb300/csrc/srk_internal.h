@@ -1,0 +1,65 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "srk.h"
+
+struct srk_graph {
+  int32_t n = 0;
+  int64_t m = 0;
+  int device = 0;
+  const int32_t *row_ptr = nullptr;  // device, n+1
+  const int32_t *col = nullptr;      // device, m
+  const float *edge_w = nullptr;     // device, m or null
+  int32_t *own_row_ptr = nullptr;    // owned copies (null when borrowed)
+  int32_t *own_col = nullptr;
+  float *own_w = nullptr;
+};
+
+namespace srk {
+
+// Sample-count table of one query (Algorithm 1 lines 3-5, Algorithm 2 line 2,
+// Lemma 7).  Passed by value as a kernel parameter (stays below 4 KB).
+struct QueryTab {
+  int32_t s, n, L, N_tot;
+  uint32_t key0, key1;
+  double z;
+  int32_t P[SRK_MAX_LEN + 2];  // stratum prefix: walk r has length l iff P[l] <= r < P[l+1]
+  double a[SRK_MAX_LEN + 1];   // rounding weight a(l) = |Z_l| / |Z^_l|
+};
+static_assert(sizeof(QueryTab) <= 4096, "kernel parameter too large");
+
+// Fills `t`; returns SRK_OK or SRK_EINVAL (message set).
+int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
+                const srk_opts *opt, QueryTab *t);
+
+// Sets the thread's last-error message (printf-style) and returns `code`.
+int fail(int code, const char *fmt, ...);
+// Maps a CUDA error to SRK_ECUDA / SRK_ENOMEM with a message.
+int cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+// Library-owned stream-ordered pool of the given device.
+cudaMemPool_t pool(int device);
+// True when p is device or managed memory visible to the current device.
+bool is_device_ptr(const void *p);
+
+// RAII guard that makes `dev` current and restores the previous device.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+      cudaSetDevice(prev);
+  }
+};
+
+// SM count of the current device (cached per device).
+int sm_count(int device);
+
+}  // namespace srk

@@ -1,0 +1,620 @@
+// Single- and multi-source queries: the sqrt(c)-walk Monte Carlo estimator of
+// arXiv 2304.04015 as kernel phases on one stream.
+//
+//   a2  k_source_walks   N_tot fixed-length walks from s (Algorithm 1 lines
+//                        4-7) and the Fisher-Yates draws of the shuffle
+//   a3  k_fy_rank .. k_pairs
+//                        the Fisher-Yates permutation sigma (Section 4.1(b),
+//                        Section 5.2), resolved in parallel (see k_pairs), and
+//                        each pair's step cap min(l2, steps of source walk)
+//       k_rows, k_hit_table
+//                        pairs sorted by cap (descending) and the step-major
+//                        hit table: row i holds, for every pair that can still
+//                        meet at step i, the source walk's node at step i
+//   a4+a5 k_target_walks the hot loop: every target walks its pairs, detects
+//                        the first meeting (Lemma 2, Algorithm 2, Section 5.5)
+//                        and writes count, weight sum and score
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "srk_device.cuh"
+#include "srk_internal.h"
+
+namespace srk {
+
+constexpr int kSmallWords = 4 * (SRK_MAX_LEN + 2);  // cap_hist, cnt, R, cursor
+
+// Layout of the small control block (int32 words), followed by 4 uint64
+// counters: [0] target steps, [1] source steps.
+struct Small {
+  int32_t *cap_hist;  // pairs per cap value 1..L
+  int32_t *cnt;       // cnt[i] = pairs with cap >= i (i = 1..L+1)
+  int32_t *R;         // R[i] = start of hit-table row i
+  int32_t *cursor;    // next free slot of each cap group
+  unsigned long long *ctr;
+};
+
+__device__ __forceinline__ Small small_view(int32_t *base) {
+  Small s;
+  s.cap_hist = base;
+  s.cnt = base + (SRK_MAX_LEN + 2);
+  s.R = base + 2 * (SRK_MAX_LEN + 2);
+  s.cursor = base + 3 * (SRK_MAX_LEN + 2);
+  s.ctr = reinterpret_cast<unsigned long long *>(base + kSmallWords);
+  return s;
+}
+
+// ---------------------------------------------------------------- step a2 --
+// Walk r of the source has length l = stratum(r).  Step i >= 1 draws 64 bits
+// from Philox counter ((i-1)>>1, r, s, s), word pair 2*((i-1)&1) (high, low),
+// and moves to I(x)[floor(R * |I(x)| / 2^64)]; it stops early at a node with
+// no in-neighbours.  The same thread computes Fisher-Yates draw t = r,
+// k_t = floor(R * (t+1) / 2^64) with R from counter (t>>1, ~0, ~0, s).
+__global__ void __launch_bounds__(256)
+k_source_walks(const int32_t *__restrict__ row_ptr,
+               const int32_t *__restrict__ col, const __grid_constant__ QueryTab tab,
+               int32_t *__restrict__ spos, int32_t *__restrict__ seff,
+               int32_t *__restrict__ kdraw, int32_t *__restrict__ grp_cnt,
+               int32_t *__restrict__ small_base) {
+  __shared__ int32_t P[SRK_MAX_LEN + 2];
+  for (int i = threadIdx.x; i <= tab.L + 1; i += blockDim.x) P[i] = tab.P[i];
+  __syncthreads();
+  const RoundKeys rk = round_keys(tab.key0, tab.key1);
+  const int Ls = tab.L > 0 ? tab.L : 1;
+  const uint32_t s = (uint32_t)tab.s;
+  unsigned long long steps = 0;
+  for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < tab.N_tot;
+       r += gridDim.x * blockDim.x) {
+    grp_cnt[r] = 0;
+    uint32_t x0, x1, x2, x3;
+    if (r >= 1) {
+      philox(rk, (uint32_t)r >> 1, 0xFFFFFFFFu, 0xFFFFFFFFu, s, x0, x1, x2, x3);
+      const uint32_t hi = (r & 1) ? x2 : x0, lo = (r & 1) ? x3 : x1;
+      kdraw[r] = (int32_t)draw_index(hi, lo, (uint32_t)r + 1u);
+    } else {
+      kdraw[0] = 0;
+    }
+    const int len = stratum_of(P, tab.L, r);
+    int32_t v = tab.s;
+    int eff = len;
+    int32_t *out = spos + (int64_t)r * Ls;
+    for (int i = 1; i <= len; ++i) {
+      const int32_t beg = row_ptr[v];
+      const int32_t deg = row_ptr[v + 1] - beg;
+      if (deg == 0) { eff = i - 1; break; }
+      if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
+      const uint32_t hi = (i & 1) ? x0 : x2, lo = (i & 1) ? x1 : x3;
+      v = col[beg + (int32_t)draw_index(hi, lo, (uint32_t)deg)];
+      out[i - 1] = v;
+    }
+    seff[r] = eff;
+    steps += (unsigned long long)eff;
+  }
+  // source-step total (one atomic per warp)
+  for (int off = 16; off > 0; off >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, off);
+  if ((threadIdx.x & 31) == 0 && steps)
+    atomicAdd(small_view(small_base).ctr + 1, steps);
+}
+
+// ---------------------------------------------------------------- step a3 --
+// The permutation sigma of the sequential Fisher-Yates loop "for t = N-1
+// down to 1: swap(sigma[t], sigma[k_t])" is resolved in parallel.  Position
+// t >= 1 is final after step t and receives the value that position k_t held
+// just before step t.  Position p (p <= t) was last written before step t by
+// the step t' = min{t' > t : k_t' = p}, which moved in the value position t'
+// held before step t'; if no such step exists it still holds p.  Following
+// these links gives sigma[t] (sigma[0]: the value of position 0 after all
+// steps).  Steps are grouped by k (counting sort) to find the links.
+
+__global__ void k_fy_rank(const int32_t *__restrict__ kdraw, int32_t *grp_cnt,
+                          int32_t *__restrict__ rank, int32_t N) {
+  for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < N;
+       t += gridDim.x * blockDim.x)
+    if (t >= 1) rank[t] = atomicAdd(&grp_cnt[kdraw[t]], 1);
+}
+
+// Exclusive scan of cnt[0..N) into off[0..N], one block of 1024 threads.
+__global__ void __launch_bounds__(1024)
+k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off, int32_t N) {
+  __shared__ int32_t warp_sum[32];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < N; base += 4096) {
+    const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+    int32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (i0 + k < N) ? cnt[i0 + k] : 0;
+    const int32_t local = v[0] + v[1] + v[2] + v[3];
+    int32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t ws = warp_sum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sum[lane] = ws;  // inclusive over warps
+    }
+    __syncthreads();
+    int32_t run = carry + (wid ? warp_sum[wid - 1] : 0) + incl - local;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (i0 + k < N) off[i0 + k] = run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = run;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[N] = carry;
+}
+
+__global__ void k_fy_scatter(const int32_t *__restrict__ kdraw,
+                             const int32_t *__restrict__ off,
+                             const int32_t *__restrict__ rank,
+                             int32_t *__restrict__ items, int32_t N) {
+  for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < N;
+       t += gridDim.x * blockDim.x)
+    if (t >= 1) items[off[kdraw[t]] + rank[t]] = t;
+}
+
+// Per group q = {t : k_t = q}: sort ascending, first[q] = its smallest step,
+// succ[t] = the next larger step of t's group (-1 for the largest).
+__global__ void k_fy_groups(const int32_t *__restrict__ off,
+                            int32_t *__restrict__ items,
+                            int32_t *__restrict__ first,
+                            int32_t *__restrict__ succ, int32_t N) {
+  for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < N;
+       q += gridDim.x * blockDim.x) {
+    const int32_t b = off[q], e = off[q + 1];
+    for (int32_t i = b + 1; i < e; ++i) {  // insertion sort (groups are tiny)
+      const int32_t x = items[i];
+      int32_t k = i - 1;
+      while (k >= b && items[k] > x) { items[k + 1] = items[k]; --k; }
+      items[k + 1] = x;
+    }
+    first[q] = (e > b) ? items[b] : -1;
+    for (int32_t i = b; i < e; ++i) succ[items[i]] = (i + 1 < e) ? items[i + 1] : -1;
+  }
+}
+
+// sigma[j] by following the links, then the pair's step cap
+// cap_j = min(l2 = stratum(j), steps taken by source walk sigma[j]);
+// pairs with cap >= 1 are counted per cap value.
+__global__ void __launch_bounds__(256)
+k_pairs(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ kdraw,
+        const int32_t *__restrict__ first, const int32_t *__restrict__ succ,
+        const int32_t *__restrict__ seff, int32_t *__restrict__ sigma,
+        int32_t *__restrict__ small_base) {
+  __shared__ int32_t P[SRK_MAX_LEN + 2];
+  __shared__ int32_t hist[SRK_MAX_LEN + 2];
+  for (int i = threadIdx.x; i <= tab.L + 1; i += blockDim.x) {
+    P[i] = tab.P[i];
+    hist[i] = 0;
+  }
+  __syncthreads();
+  const int32_t N = tab.N_tot;
+  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < N;
+       j += gridDim.x * blockDim.x) {
+    int32_t p, h;
+    if (j == 0) {
+      p = 0;
+      h = first[0];
+    } else {
+      p = kdraw[j];
+      h = succ[j];
+    }
+    for (int32_t guard = 0; h >= 0 && guard < N; ++guard) {
+      p = h;
+      const int32_t f = first[p];
+      h = (f == p) ? succ[p] : f;  // next write of position p after step p
+    }
+    sigma[j] = p;
+    const int l2 = stratum_of(P, tab.L, j);
+    const int32_t cap = min(l2, seff[p]);
+    if (cap >= 1) atomicAdd(&hist[cap], 1);
+  }
+  __syncthreads();
+  Small sm = small_view(small_base);
+  for (int i = threadIdx.x; i <= tab.L + 1; i += blockDim.x)
+    if (hist[i]) atomicAdd(&sm.cap_hist[i], hist[i]);
+}
+
+// Hit-table geometry: pairs sorted by cap, descending.  Row i (i = 1..L) has
+// cnt[i] = #pairs with cap >= i entries and starts at R[i].
+__global__ void k_rows(int L, int32_t *__restrict__ small_base) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Small sm = small_view(small_base);
+  int32_t c = 0;
+  sm.cnt[L + 1] = 0;
+  for (int i = L; i >= 1; --i) {
+    sm.cursor[i] = c;  // cap-i pairs follow all pairs with a larger cap
+    c += sm.cap_hist[i];
+    sm.cnt[i] = c;
+  }
+  int32_t r = 0;
+  for (int i = 1; i <= L + 1; ++i) {
+    sm.R[i] = r;
+    if (i <= L) r += sm.cnt[i];
+  }
+  sm.cnt[0] = c;
+  sm.R[0] = 0;
+}
+
+// Places every pair with cap >= 1 in its cap group and fills its column of the
+// hit table with the source walk's nodes at steps 1..cap.  The pair's Lemma 7
+// weight is round(a(l1) a(l2) 2^32) with l1 the source walk's length.
+__global__ void __launch_bounds__(256)
+k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ sigma,
+            const int32_t *__restrict__ seff, const int32_t *__restrict__ spos,
+            int32_t *__restrict__ small_base, int32_t *__restrict__ pair_j,
+            unsigned long long *__restrict__ pair_w, int32_t *__restrict__ Hc) {
+  __shared__ int32_t P[SRK_MAX_LEN + 2];
+  __shared__ int32_t R[SRK_MAX_LEN + 2];
+  Small sm = small_view(small_base);
+  for (int i = threadIdx.x; i <= tab.L + 1; i += blockDim.x) {
+    P[i] = tab.P[i];
+    R[i] = sm.R[i];
+  }
+  __syncthreads();
+  const int Ls = tab.L > 0 ? tab.L : 1;
+  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < tab.N_tot;
+       j += gridDim.x * blockDim.x) {
+    const int32_t w = sigma[j];
+    const int l2 = stratum_of(P, tab.L, j);
+    const int32_t cap = min(l2, seff[w]);
+    if (cap < 1) continue;
+    const int l1 = stratum_of(P, tab.L, w);
+    const int32_t a = atomicAdd(&sm.cursor[cap], 1);
+    pair_j[a] = j;
+    pair_w[a] = __double2ull_rn(tab.a[l1] * tab.a[l2] * 4294967296.0);
+    const int32_t *src = spos + (int64_t)w * Ls;
+    for (int i = 1; i <= cap; ++i) Hc[R[i] + a] = src[i - 1];
+  }
+}
+
+// -------------------------------------------------------------- steps a4-a5 --
+// One warp per target u at a time (grid-stride over targets), lanes over the
+// pairs a = lane, lane+32, ... of the cap-sorted list.  Pair a (original index
+// j) walks from u: step i draws from Philox counter ((i-1)>>1, j, u, s); the
+// walk meets when its node equals row i of the hit table, ends after cap
+// steps (a >= cnt[i+1]) or at a node without in-neighbours.  The first
+// meeting adds 1 to the count and the pair's weight to W_u; the warp then
+// reduces and writes count, W and s~(s,u) = W 2^-32 / z (s~(s,s) = 1).
+struct TargetArgs {
+  const int32_t *row_ptr;
+  const int32_t *col;
+  int32_t n, s, L;
+  uint32_t key0, key1;
+  double z;
+  const int32_t *small_base;
+  const int32_t *pair_j;
+  const unsigned long long *pair_w;
+  const int32_t *Hc;
+  double *scores;
+  uint32_t *counts;
+  unsigned long long *wsums;
+  uint32_t *steps_per_target;
+  unsigned long long *steps_total;
+};
+
+__global__ void __launch_bounds__(256)
+k_target_walks(const __grid_constant__ TargetArgs A) {
+  __shared__ int32_t cnt[SRK_MAX_LEN + 2];
+  __shared__ int32_t R[SRK_MAX_LEN + 2];
+  {
+    const int32_t *cb = A.small_base + (SRK_MAX_LEN + 2);
+    const int32_t *rb = A.small_base + 2 * (SRK_MAX_LEN + 2);
+    for (int i = threadIdx.x; i <= A.L + 1; i += blockDim.x) {
+      cnt[i] = cb[i];
+      R[i] = rb[i];
+    }
+  }
+  __syncthreads();
+  const RoundKeys rk = round_keys(A.key0, A.key1);
+  const int lane = threadIdx.x & 31;
+  const int32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int32_t n_pairs = cnt[1];
+  const uint32_t s = (uint32_t)A.s;
+  const int32_t *__restrict__ row_ptr = A.row_ptr;
+  const int32_t *__restrict__ col = A.col;
+  const int32_t *__restrict__ Hc = A.Hc;
+  const int32_t *__restrict__ pair_j = A.pair_j;
+  unsigned long long warp_steps = 0;
+  for (int32_t u = warp; u < A.n; u += nwarps) {
+    uint32_t c = 0, st = 0;
+    unsigned long long W = 0;
+    if (u != A.s) {
+      const int32_t beg_u = row_ptr[u];
+      const int32_t deg_u = row_ptr[u + 1] - beg_u;
+      if (deg_u > 0) {
+        for (int32_t a = lane; a < n_pairs; a += 32) {
+          const uint32_t j = (uint32_t)pair_j[a];
+          int32_t beg = beg_u, deg = deg_u;
+          uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+          for (int i = 1; i <= A.L; ++i) {
+            if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, j, (uint32_t)u, s, x0, x1, x2, x3);
+            const uint32_t hi = (i & 1) ? x0 : x2, lo = (i & 1) ? x1 : x3;
+            const int32_t x = col[beg + (int32_t)draw_index(hi, lo, (uint32_t)deg)];
+            ++st;
+            if (x == Hc[R[i] + a]) {
+              ++c;
+              W += A.pair_w[a];
+              break;
+            }
+            if (a >= cnt[i + 1]) break;  // cap reached
+            beg = row_ptr[x];
+            deg = row_ptr[x + 1] - beg;
+            if (deg == 0) break;  // no in-neighbours: the walk ends
+          }
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      c += __shfl_xor_sync(0xffffffffu, c, off);
+      st += __shfl_xor_sync(0xffffffffu, st, off);
+      W += __shfl_xor_sync(0xffffffffu, W, off);
+    }
+    if (lane == 0) {
+      A.scores[u] = (u == A.s) ? 1.0 : (double)W * 2.3283064365386963e-10 / A.z;
+      if (A.counts) A.counts[u] = c;
+      if (A.wsums) A.wsums[u] = W;
+      if (A.steps_per_target) A.steps_per_target[u] = st;
+      warp_steps += st;
+    }
+  }
+  if (lane == 0 && warp_steps) atomicAdd(A.steps_total, warp_steps);
+}
+
+// ------------------------------------------------------------ host side --
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Workspace {
+  int32_t *spos, *seff, *kdraw, *grp_cnt, *rank, *grp_off, *items, *first,
+      *succ, *sigma, *pair_j, *Hc, *small;
+  unsigned long long *pair_w;
+  size_t bytes;
+};
+
+static size_t plan(const QueryTab &t, Workspace *w, char *base) {
+  const size_t N = (size_t)t.N_tot;
+  const size_t Ls = (size_t)(t.L > 0 ? t.L : 1);
+  size_t hc = 0;
+  for (int l = 1; l <= t.L; ++l) hc += (size_t)l * (size_t)(t.P[l + 1] - t.P[l]);
+  if (hc == 0) hc = 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char *p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  w->spos = (int32_t *)take(4 * N * Ls);
+  w->seff = (int32_t *)take(4 * N);
+  w->kdraw = (int32_t *)take(4 * N);
+  w->grp_cnt = (int32_t *)take(4 * N);
+  w->rank = (int32_t *)take(4 * N);
+  w->grp_off = (int32_t *)take(4 * (N + 1));
+  w->items = (int32_t *)take(4 * N);
+  w->first = (int32_t *)take(4 * N);
+  w->succ = (int32_t *)take(4 * N);
+  w->sigma = (int32_t *)take(4 * N);
+  w->pair_j = (int32_t *)take(4 * N);
+  w->pair_w = (unsigned long long *)take(8 * N);
+  w->Hc = (int32_t *)take(4 * hc);
+  w->small = (int32_t *)take(4 * kSmallWords + 64);
+  w->bytes = off;
+  return off;
+}
+
+static int grid_for(int64_t work, int threads, int device) {
+  const int64_t want = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm_count(device) * 8;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+}
+
+static int target_grid(int device) {
+  static int blocks_per_sm[64] = {};
+  int b = (device >= 0 && device < 64) ? blocks_per_sm[device] : 0;
+  if (!b) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks, 256, 0) !=
+            cudaSuccess || b < 1)
+      b = 1;
+    if (device >= 0 && device < 64) blocks_per_sm[device] = b;
+  }
+  return sm_count(device) * b;
+}
+
+struct Outputs {
+  double *scores;
+  uint32_t *counts;
+  unsigned long long *wsums;
+  uint32_t *steps;
+};
+
+// Enqueues one query on `st` with device-resident outputs `o`.  Workspace
+// `w` (already carved) must hold plan(t) bytes.
+static int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
+                         const Outputs &o, cudaStream_t st,
+                         const cudaEvent_t *timing = nullptr) {
+  const int dev = g->device;
+  const int N = t.N_tot;
+  const int gN = grid_for(N, 256, dev);
+  cudaError_t e = cudaMemsetAsync(w.small, 0, 4 * kSmallWords + 64, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clearing query counters");
+  k_source_walks<<<gN, 256, 0, st>>>(g->row_ptr, g->col, t, w.spos, w.seff,
+                                     w.kdraw, w.grp_cnt, w.small);
+  k_fy_rank<<<gN, 256, 0, st>>>(w.kdraw, w.grp_cnt, w.rank, N);
+  k_scan<<<1, 1024, 0, st>>>(w.grp_cnt, w.grp_off, N);
+  k_fy_scatter<<<gN, 256, 0, st>>>(w.kdraw, w.grp_off, w.rank, w.items, N);
+  k_fy_groups<<<gN, 256, 0, st>>>(w.grp_off, w.items, w.first, w.succ, N);
+  k_pairs<<<gN, 256, 0, st>>>(t, w.kdraw, w.first, w.succ, w.seff, w.sigma, w.small);
+  k_rows<<<1, 32, 0, st>>>(t.L, w.small);
+  k_hit_table<<<gN, 256, 0, st>>>(t, w.sigma, w.seff, w.spos, w.small, w.pair_j,
+                                  w.pair_w, w.Hc);
+  TargetArgs A;
+  A.row_ptr = g->row_ptr;
+  A.col = g->col;
+  A.n = g->n;
+  A.s = t.s;
+  A.L = t.L;
+  A.key0 = t.key0;
+  A.key1 = t.key1;
+  A.z = t.z;
+  A.small_base = w.small;
+  A.pair_j = w.pair_j;
+  A.pair_w = w.pair_w;
+  A.Hc = w.Hc;
+  A.scores = o.scores;
+  A.counts = o.counts;
+  A.wsums = o.wsums;
+  A.steps_per_target = o.steps;
+  A.steps_total = reinterpret_cast<unsigned long long *>(w.small + kSmallWords);
+  if (timing) cudaEventRecord(timing[0], st);
+  k_target_walks<<<target_grid(dev), 256, 0, st>>>(A);
+  if (timing) cudaEventRecord(timing[1], st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return SRK_OK;
+}
+
+// Reads back the counters of the small block into `stats` (synchronous).
+static int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
+                      srk_stats *stats, bool accumulate) {
+  unsigned long long ctr[2] = {0, 0};
+  int32_t active = 0;
+  cudaError_t e = cudaMemcpyAsync(ctr, w.small + kSmallWords, sizeof ctr,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&active, w.small + (SRK_MAX_LEN + 2) + 1, sizeof active,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading query statistics");
+  if (!accumulate) memset(stats, 0, sizeof *stats);
+  stats->z = t.z;
+  stats->L = t.L;
+  stats->n_walks = t.N_tot;
+  stats->n_active_pairs += active;
+  stats->target_steps += ctr[0];
+  stats->source_steps += ctr[1];
+  return SRK_OK;
+}
+
+}  // namespace srk
+
+using namespace srk;
+
+extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
+                                 double eps, uint64_t seed, const srk_opts *opt,
+                                 double *scores, uint32_t *meet_counts,
+                                 uint64_t *weight_sums, void *cuda_stream) {
+  clear_error();
+  if (!g) return fail(SRK_EINVAL, "null graph");
+  if (!scores) return fail(SRK_EINVAL, "scores is null");
+  if (opt && opt->flags != 0) return fail(SRK_EINVAL, "opts.flags must be 0");
+  QueryTab t;
+  int rc = build_table(g->n, s, c, eps, seed, opt, &t);
+  if (rc) return rc;
+  DeviceGuard guard(g->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)g->n;
+  uint32_t *step_counts = opt ? opt->step_counts : nullptr;
+  const bool d_scores = is_device_ptr(scores);
+  const bool d_counts = !meet_counts || is_device_ptr(meet_counts);
+  const bool d_wsums = !weight_sums || is_device_ptr(weight_sums);
+  const bool d_steps = !step_counts || is_device_ptr(step_counts);
+  Workspace w;
+  size_t ws = plan(t, &w, nullptr);
+  const size_t ws_core = ws;
+  const size_t o_scores = ws;
+  if (!d_scores) ws += align_up(8 * n);
+  const size_t o_counts = ws;
+  if (!d_counts) ws += align_up(4 * n);
+  const size_t o_wsums = ws;
+  if (!d_wsums) ws += align_up(8 * n);
+  const size_t o_steps = ws;
+  if (!d_steps) ws += align_up(4 * n);
+  cudaMemPool_t mp = pool(g->device);
+  if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
+  char *base = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&base, ws, mp, st);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+  plan(t, &w, base);
+  (void)ws_core;
+  Outputs o;
+  o.scores = d_scores ? scores : (double *)(base + o_scores);
+  o.counts = d_counts ? meet_counts : (uint32_t *)(base + o_counts);
+  o.wsums = d_wsums ? (unsigned long long *)weight_sums
+                    : (unsigned long long *)(base + o_wsums);
+  o.steps = d_steps ? step_counts : (uint32_t *)(base + o_steps);
+  rc = enqueue_query(g, t, w, o, st,
+                     opt ? (const cudaEvent_t *)opt->timing_events : nullptr);
+  bool host_out = !d_scores || !d_counts || !d_wsums || !d_steps;
+  if (!rc) {
+    if (!d_scores) e = cudaMemcpyAsync(scores, o.scores, 8 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !d_counts)
+      e = cudaMemcpyAsync(meet_counts, o.counts, 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !d_wsums)
+      e = cudaMemcpyAsync(weight_sums, o.wsums, 8 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !d_steps)
+      e = cudaMemcpyAsync(step_counts, o.steps, 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copying results to the host");
+  }
+  if (!rc && opt && opt->stats) rc = read_stats(t, w, st, opt->stats, false);
+  cudaFreeAsync(base, st);
+  if (!rc && host_out) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "srk_single_source");
+  }
+  return rc;
+}
+
+extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
+                                int32_t k, double c, const double *eps,
+                                uint64_t seed, const srk_opts *opt,
+                                double *scores, uint32_t *meet_counts,
+                                void *cuda_stream) {
+  clear_error();
+  if (!g) return fail(SRK_EINVAL, "null graph");
+  if (k < 0) return fail(SRK_EINVAL, "k = %d is negative", k);
+  if (k == 0) return SRK_OK;
+  if (!sources || !eps || !scores) return fail(SRK_EINVAL, "null argument");
+  if (opt && opt->step_counts)
+    return fail(SRK_EINVAL, "step_counts is not supported by srk_multi_source");
+  srk_opts local;
+  memset(&local, 0, sizeof local);
+  local.L_override = -1;
+  if (opt) local = *opt;
+  srk_stats total;
+  memset(&total, 0, sizeof total);
+  const size_t n = (size_t)g->n;
+  for (int32_t i = 0; i < k; ++i) {
+    srk_stats one;
+    local.stats = (opt && opt->stats) ? &one : nullptr;
+    int rc = srk_single_source(g, sources[i], c, eps[i], seed, &local,
+                               scores + (size_t)i * n,
+                               meet_counts ? meet_counts + (size_t)i * n : nullptr,
+                               nullptr, cuda_stream);
+    if (rc) return fail(rc, "source %d (index %d): %s", sources[i], i, srk_last_error());
+    if (opt && opt->stats) {
+      total.z = one.z;
+      total.L = one.L;
+      total.n_walks += one.n_walks;
+      total.n_active_pairs += one.n_active_pairs;
+      total.source_steps += one.source_steps;
+      total.target_steps += one.target_steps;
+    }
+  }
+  if (opt && opt->stats) *opt->stats = total;
+  return SRK_OK;
+}

@@ -18,7 +18,7 @@ Recipes (the paper has no datasets; these stand in for its graphs):
 * ``rmat_in_csr``: R-MAT with 2**scale nodes and edge_factor * 2**scale edge
   draws.  Each draw descends ``scale`` levels of the adjacency matrix, choosing
   quadrant (row bit, column bit) = (0,0), (0,1), (1,0), (1,1) with
-  probabilities (a, b, c, d).  Row = source, column = target of the directed
+  probabilities (a, b, c, d) (one float32 uniform per level).  Row = source, column = target of the directed
   edge source -> target, so the source becomes an in-neighbour of the target.
   Self-loops are dropped, duplicates removed, node ids are not permuted.
 * ``uniform_sources``: distinct nodes drawn uniformly.
@@ -45,7 +45,7 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray):
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
     keep = src != dst
-    key = np.unique(dst[keep] * n + src[keep])  # sorted by (dst, src), deduped
+    key = _sorted_unique(dst[keep] * n + src[keep])  # sorted by (dst, src), deduped
     dst_s = key // n
     col = (key - dst_s * n).astype(np.int32)
     counts = np.bincount(dst_s, minlength=n).astype(np.int64)
@@ -75,36 +75,50 @@ def er_in_csr(n: int, mean_in_degree: float = 5.0, seed: int = 1):
     return row_ptr.astype(np.int32), col
 
 
+def _sorted_unique(key: np.ndarray) -> np.ndarray:
+    key.sort()
+    if key.size == 0:
+        return key
+    keep = np.empty(key.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(key[1:], key[:-1], out=keep[1:])
+    return key[keep]
+
+
 def rmat_in_csr(scale: int, edge_factor: int = 16,
                 abcd=(0.57, 0.19, 0.19, 0.05), seed: int = 1,
-                chunk: int = 1 << 24):
-    """R-MAT graph (see module doc), returned as an in-neighbour CSR."""
+                chunk: int = 1 << 25):
+    """R-MAT graph (see module doc), returned as an in-neighbour CSR.
+
+    Each level draws one float32 uniform r per edge and picks the quadrant by
+    the float32 thresholds a, a+b, a+b+c.
+    """
     a, b, c, d = abcd
     if abs(a + b + c + d - 1.0) > 1e-9:
         raise ValueError("R-MAT probabilities must sum to 1")
     n = 1 << scale
     n_draws = edge_factor * n
     rng = np.random.default_rng(seed)
+    t_a, t_ab, t_abc = np.float32(a), np.float32(a + b), np.float32(a + b + c)
     keys = []
     done = 0
-    t_ab, t_abc = a + b, a + b + c
     while done < n_draws:
         e = min(chunk, n_draws - done)
         src = np.zeros(e, dtype=np.int64)
         dst = np.zeros(e, dtype=np.int64)
         for level in range(scale):
-            r = rng.random(e)
-            bit = np.int64(1) << np.int64(scale - 1 - level)
+            r = rng.random(e, dtype=np.float32)
+            sh = scale - 1 - level
             row = r >= t_ab
-            colb = ((r >= a) & (r < t_ab)) | (r >= t_abc)
-            src |= np.where(row, bit, 0)
-            dst |= np.where(colb, bit, 0)
+            colb = ((r >= t_a) & (r < t_ab)) | (r >= t_abc)
+            src += row.astype(np.int64) << sh
+            dst += colb.astype(np.int64) << sh
         keep = src != dst
-        keys.append(np.unique(dst[keep] * n + src[keep]))
+        keys.append(_sorted_unique(dst[keep] * n + src[keep]))
         done += e
-    key = np.unique(np.concatenate(keys)) if len(keys) > 1 else keys[0]
-    dst_s = key // n
-    col = (key - dst_s * n).astype(np.int32)
+    key = _sorted_unique(np.concatenate(keys)) if len(keys) > 1 else keys[0]
+    dst_s = key >> scale
+    col = (key & (n - 1)).astype(np.int32)
     counts = np.bincount(dst_s, minlength=n).astype(np.int64)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])

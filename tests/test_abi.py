@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol ``include/srk.h``
+declares; the Python binding exposes the same names (CPU only: no compute
+call is made without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "srk.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(srk_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_04015_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("srk_graph_load", "srk_graph_free", "srk_single_source",
+                     "srk_multi_source", "srk_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_has_the_same_names(lib):
+    import paper_2304_04015_gb300 as srk
+    for name in declared_functions():
+        assert callable(getattr(srk, name)), name
+
+
+def test_last_error_starts_empty(lib):
+    lib.srk_last_error.restype = ctypes.c_char_p
+    assert lib.srk_last_error() in (b"",)
+
+
+def test_graph_load_rejects_bad_arguments_without_touching_the_device(lib):
+    # argument checks run before any CUDA call
+    import paper_2304_04015_gb300 as srk
+    out = ctypes.c_void_p()
+    assert lib.srk_graph_load(None, None, 0, 0, 0, None, ctypes.byref(out)) == srk.SRK_EINVAL
+    assert lib.srk_graph_load(None, None, 5, -1, 0, None, ctypes.byref(out)) == srk.SRK_EINVAL
+    assert lib.srk_graph_load(None, None, 5, 0, 0, None, None) == srk.SRK_EINVAL
+    assert b"out is null" in lib.srk_last_error()
+    assert lib.srk_single_source(None, 0, ctypes.c_double(0.6), ctypes.c_double(0.1),
+                                 ctypes.c_uint64(1), None, None, None, None, None) == srk.SRK_EINVAL
+
+
+def test_build_entry_point():
+    import __graft_entry__ as g
+    g.build()

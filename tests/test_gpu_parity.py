@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Counts, weight sums and step counts are integers: they must match bit for
+bit.  Scores are W 2^-32 / z evaluated in IEEE FP64 on both sides, so they
+must match bit for bit too.  Accuracy against exact SimRank is Theorem 6's
+bound |s~ - s| <= eps on the small configuration.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+C = 0.6
+
+
+@pytest.fixture(scope="module")
+def srk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as m
+    return m
+
+
+@functools.lru_cache(maxsize=None)
+def er_graph(n, deg, seed):
+    from srk_inputs import er_in_csr
+    return er_in_csr(n, deg, seed=seed)
+
+
+@functools.lru_cache(maxsize=None)
+def rmat_graph(scale, seed=1):
+    from srk_inputs import rmat_in_csr
+    return rmat_in_csr(scale, seed=seed)
+
+
+def gpu_query(srk, rp, col, s, eps, seed, device_outputs=True, **kw):
+    import torch
+    dev = torch.device("cuda:0")
+    n = rp.size - 1
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    stats = srk.SrkStats()
+    try:
+        if device_outputs:
+            scores = torch.empty(n, dtype=torch.float64, device=dev)
+            counts = torch.empty(n, dtype=torch.int32, device=dev)
+            wsums = torch.empty(n, dtype=torch.int64, device=dev)
+            steps = torch.empty(n, dtype=torch.int32, device=dev)
+            srk.srk_single_source(g, s, C, eps, seed, scores, counts, wsums,
+                                  step_counts=steps, stats=stats, **kw)
+            torch.cuda.synchronize()
+            out = (scores.cpu().numpy(), counts.cpu().numpy().view(np.uint32),
+                   wsums.cpu().numpy().view(np.uint64), steps.cpu().numpy().view(np.uint32))
+        else:
+            scores = np.empty(n, dtype=np.float64)
+            counts = np.empty(n, dtype=np.uint32)
+            wsums = np.empty(n, dtype=np.uint64)
+            steps = np.empty(n, dtype=np.uint32)
+            srk.srk_single_source(g, s, C, eps, seed, scores, counts, wsums,
+                                  step_counts=steps, stats=stats, **kw)
+            out = (scores, counts, wsums, steps)
+    finally:
+        g.close()
+    return out + (stats,)
+
+
+def oracle_query(rp, col, s, eps, seed, targets=None, **kw):
+    from oracle import sampler
+    return sampler.run(rp, col, rp.size - 1, s, C, eps, seed, targets=targets, **kw)
+
+
+def assert_parity(gpu, ref, targets=None):
+    scores, counts, wsums, steps, stats = gpu
+    sel = slice(None) if targets is None else targets
+    assert np.array_equal(counts[sel], ref.count)
+    assert np.array_equal(wsums[sel], ref.wsum)
+    assert np.array_equal(steps[sel].astype(np.uint64), ref.steps)
+    assert np.array_equal(scores[sel], ref.scores)
+    assert stats.n_walks == ref.table.N_tot and stats.L == ref.table.L
+    assert stats.z == ref.table.z
+    assert stats.source_steps == ref.source_steps
+    if targets is None:
+        assert stats.target_steps == int(ref.steps.sum())
+
+
+TINY = dict(z_override=2000.0, L_override=32)
+
+
+def test_tiny_configuration_bit_exact(srk):
+    # ER n=1000, Poisson(5) in-degrees, source 0, c=0.6, eps=0.1, 2000 pairs, L=32
+    rp, col = er_graph(1000, 5.0, 1)
+    for seed in (1, 2):
+        gpu = gpu_query(srk, rp, col, 0, 0.1, seed, **TINY)
+        ref = oracle_query(rp, col, 0, 0.1, seed, **TINY)
+        assert_parity(gpu, ref)
+        assert ref.count.sum() > 1000     # the case exercises meetings
+
+
+def test_tiny_configuration_within_eps_of_exact(srk):
+    from oracle import exact
+    rp, col = er_graph(1000, 5.0, 1)
+    S, _ = exact.jeh_widom(rp, col, 1000, C)
+    scores = gpu_query(srk, rp, col, 0, 0.1, 1, **TINY)[0]
+    assert scores[0] == 1.0
+    assert np.abs(scores - S[0]).max() <= 0.1
+
+
+def test_host_and_device_outputs_agree(srk):
+    rp, col = er_graph(1000, 5.0, 1)
+    a = gpu_query(srk, rp, col, 3, 0.1, 9, device_outputs=True, **TINY)
+    b = gpu_query(srk, rp, col, 3, 0.1, 9, device_outputs=False, **TINY)
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("pick", ["hub", "uniform", "zero_in_degree", "leaf"])
+def test_rmat16_paper_parameters_bit_exact(srk, pick):
+    rp, col = rmat_graph(16)
+    deg = np.diff(rp)
+    s = {"hub": int(np.argmax(deg)),
+         "uniform": 12345,
+         "zero_in_degree": int(np.flatnonzero(deg == 0)[7]),
+         "leaf": int(np.flatnonzero(deg == 1)[3])}[pick]
+    gpu = gpu_query(srk, rp, col, s, 0.05, 17)
+    ref = oracle_query(rp, col, s, 0.05, 17)
+    assert_parity(gpu, ref)
+
+
+def test_rmat20_eps002_sampled_targets_bit_exact(srk):
+    # the benchmark's workload and launch configuration: R-MAT scale 20,
+    # c=0.6, eps=0.02, sources from the uniform list; every output of the full
+    # query is computed, the oracle re-computes a sample of targets one by one
+    from srk_inputs import uniform_sources
+    rp, col = rmat_graph(20)
+    n = rp.size - 1
+    deg = np.diff(rp)
+    sources = uniform_sources(n, 64, seed=2)
+    rng = np.random.default_rng(5)
+    for s in (int(sources[0]), int(np.argmax(deg))):
+        gpu = gpu_query(srk, rp, col, s, 0.02, 2024)
+        targets = np.unique(np.concatenate([
+            rng.choice(n, 1500, replace=False),
+            np.argsort(-deg)[:50],                  # hubs
+            [s, 0, n - 1]])).astype(np.int32)
+        ref = oracle_query(rp, col, s, 0.02, 2024, targets=targets)
+        assert_parity(gpu, ref, targets)
+        scores = gpu[0]
+        assert np.all(scores[deg == 0][scores[deg == 0] != 1.0] == 0.0)
+        assert np.all((scores >= 0.0) & (scores <= 1.0))
+
+
+def test_edge_cases(srk):
+    rp, col = er_graph(200, 3.0, 4)
+    deg = np.diff(rp)
+    # L = 0: only length-0 walks, no step can meet
+    gpu = gpu_query(srk, rp, col, 1, 0.5, 3, z_override=100.0, L_override=0)
+    assert gpu[1].sum() == 0 and gpu[0][1] == 1.0 and np.count_nonzero(gpu[0]) == 1
+    # source without in-neighbours
+    s = int(np.flatnonzero(deg == 0)[0])
+    gpu = gpu_query(srk, rp, col, s, 0.5, 3, z_override=300.0)
+    ref = oracle_query(rp, col, s, 0.5, 3, z_override=300.0)
+    assert_parity(gpu, ref)
+    # a graph with no edges at all
+    n = 40
+    rp0 = np.zeros(n + 1, dtype=np.int32)
+    col0 = np.zeros(0, dtype=np.int32)
+    gpu = gpu_query(srk, rp0, col0, 5, 0.5, 3)
+    assert gpu[1].sum() == 0 and gpu[0][5] == 1.0 and np.count_nonzero(gpu[0]) == 1
+    # the largest truncation length, with a ragged pair count
+    gpu = gpu_query(srk, rp, col, 2, 0.5, 8, z_override=777.7, L_override=srk.SRK_MAX_LEN)
+    ref = oracle_query(rp, col, 2, 0.5, 8, z_override=777.7, L_override=srk.SRK_MAX_LEN)
+    assert_parity(gpu, ref)
+    # many walks per node (N_tot > 2^17) on a small graph
+    gpu = gpu_query(srk, rp, col, 2, 0.5, 8, z_override=150000.5)
+    ref = oracle_query(rp, col, 2, 0.5, 8, z_override=150000.5)
+    assert_parity(gpu, ref)
+    # the knobs of Appendix B.5
+    gpu = gpu_query(srk, rp, col, 2, 0.3, 8, p=2.0, q=2.0)
+    ref = oracle_query(rp, col, 2, 0.3, 8, p=2.0, q=2.0)
+    assert_parity(gpu, ref)
+
+
+def test_pairs_meeting_at_every_step(srk):
+    # I(s) = I(u) = {x}, I(x) = {y}, I(y) = {x}: lockstep walks meet at step 1
+    rp = np.array([0, 1, 2, 3, 4], dtype=np.int32)
+    col = np.array([2, 2, 3, 2], dtype=np.int32)
+    gpu = gpu_query(srk, rp, col, 0, 0.9, 5, z_override=500.0, L_override=9)
+    ref = oracle_query(rp, col, 0, 0.9, 5, z_override=500.0, L_override=9)
+    assert_parity(gpu, ref)
+    assert gpu[1][1] > 0 and gpu[3][1] == gpu[1][1]   # each meeting after one step
+
+
+def test_deterministic_and_seed_sensitive(srk):
+    rp, col = rmat_graph(16)
+    a = gpu_query(srk, rp, col, 100, 0.05, 1)
+    b = gpu_query(srk, rp, col, 100, 0.05, 1)
+    c = gpu_query(srk, rp, col, 100, 0.05, 2)
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+    assert not np.array_equal(a[2], c[2])
+
+
+def test_multi_source_equals_single_queries(srk):
+    import torch
+    rp, col = rmat_graph(16)
+    n = rp.size - 1
+    sources = [0, 77, 4096, 65535]
+    eps = [0.05, 0.1, 0.08, 0.2]
+    dev = torch.device("cuda:0")
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        multi = torch.empty((4, n), dtype=torch.float64, device=dev)
+        mc = torch.empty((4, n), dtype=torch.int32, device=dev)
+        stats = srk.SrkStats()
+        srk.srk_multi_source(g, sources, C, eps, 11, multi, mc, stats=stats)
+        one = torch.empty(n, dtype=torch.float64, device=dev)
+        oc = torch.empty(n, dtype=torch.int32, device=dev)
+        total = 0
+        for i, s in enumerate(sources):
+            st = srk.SrkStats()
+            srk.srk_single_source(g, s, C, eps[i], 11, one, oc, stats=st)
+            torch.cuda.synchronize()
+            assert torch.equal(one, multi[i]) and torch.equal(oc, mc[i])
+            total += st.target_steps
+        assert stats.target_steps == total
+    finally:
+        g.close()
+
+
+def test_invalid_arguments_are_rejected(srk):
+    import torch
+    rp, col = er_graph(100, 3.0, 2)
+    dev = torch.device("cuda:0")
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    out = torch.empty(100, dtype=torch.float64, device=dev)
+    try:
+        for args in [(-1, 0.6, 0.5), (100, 0.6, 0.5), (0, 0.0, 0.5), (0, 1.0, 0.5),
+                     (0, 0.6, 0.03), (0, 0.6, 1.0)]:
+            with pytest.raises(srk.SrkError) as e:
+                srk.srk_single_source(g, args[0], args[1], args[2], 1, out)
+            assert e.value.code == srk.SRK_EINVAL
+        with pytest.raises(srk.SrkError):
+            srk.srk_single_source(g, 0, 0.6, 0.5, 1, out, z_override=1e9)  # N_tot too large
+        with pytest.raises(srk.SrkError):
+            srk.srk_single_source(g, 0, 0.6, 0.5, 1, out, L_override=srk.SRK_MAX_LEN + 1)
+        with pytest.raises(srk.SrkError):
+            srk.srk_single_source(g, 0, 0.6, 0.5, 1, out, p=0.5)
+    finally:
+        g.close()
+    # malformed CSRs are refused at load time (checked by an in-bounds kernel)
+    bad_col = col.copy()
+    bad_col[5] = 100
+    with pytest.raises(srk.SrkError) as e:
+        srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(bad_col).to(dev))
+    assert e.value.code == srk.SRK_EINVAL
+    bad_rp = rp.copy()
+    bad_rp[10], bad_rp[11] = bad_rp[11] + 1, bad_rp[10]
+    with pytest.raises(srk.SrkError):
+        srk.srk_graph_load(bad_rp, col)
