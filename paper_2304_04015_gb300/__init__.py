@@ -37,8 +37,8 @@ library_path = os.path.join(_HERE, "libsrk.so")
 
 if not os.path.exists(library_path):
     raise ImportError(
-        "libsrk.so is not built; run `python -m paper_2304_04015_gb300.build` "
-        "(needs nvcc).  There is no CPU fallback.")
+        "libsrk.so is not built; run `python paper_2304_04015_gb300/build.py` "
+        "or __graft_entry__.build() (needs nvcc).  There is no CPU fallback.")
 _lib = ctypes.CDLL(library_path)
 
 

@@ -3,8 +3,9 @@
 Each ``csrc/*.cu`` file compiles to an object in ``_build/`` in parallel; the
 objects link into ``paper_2304_04015_gb300/libsrk.so``.  Host code is built
 without floating-point contraction so the sample-count table is evaluated in
-exactly the order the source states.  Usage: ``python -m
-paper_2304_04015_gb300.build`` or ``build()``.
+exactly the order the source states.  Usage: ``python
+paper_2304_04015_gb300/build.py`` (this file does not import the package,
+whose import needs the library).
 """
 from __future__ import annotations
 

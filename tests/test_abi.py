@@ -19,8 +19,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2304_04015_gb300.build import build
-    path = build()
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
     return ctypes.CDLL(path)
 
 
