@@ -163,6 +163,32 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
                      const srk_opts *opt, double *scores,
                      uint32_t *meet_counts, void *cuda_stream);
 
+/*
+ * srk_single_source_noalloc -- srk_single_source that allocates nothing.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory while they issue queries (an application whose
+ * own allocator owns the device budget, a serving thread that must not block
+ * on or fail in the driver's allocator).  Load the graph once beforehand
+ * (SRK_DEVICE_PTRS borrows the caller's arrays); this call then makes no
+ * cudaMalloc, cudaFree, cudaMallocAsync or other allocating call.
+ *   Arguments and results are those of srk_single_source, except: scores,
+ *   meet_counts, weight_sums and opt->step_counts must be device memory
+ *   (SRK_EINVAL otherwise), and the query's scratch must fit in
+ *   SRK_NOALLOC_SCRATCH_BYTES (about 4 N_tot (L + 18) bytes; SRK_EINVAL with
+ *   the needed size otherwise).
+ *   Scratch: one static device array of SRK_NOALLOC_SCRATCH_BYTES, held on
+ *   every GPU where the library's module is loaded until the process exits.
+ *   Its address is looked up by the first call on each device (make that
+ *   first call before any stream capture).  Every call reuses the array and
+ *   clears what must start at zero; calls that overlap on the GPU (e.g. on
+ *   two streams) race on it and must be serialised by the caller.
+ */
+#define SRK_NOALLOC_SCRATCH_BYTES (16u << 20)
+int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c,
+                              double eps, uint64_t seed, const srk_opts *opt,
+                              double *scores, uint32_t *meet_counts,
+                              uint64_t *weight_sums, void *cuda_stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char *srk_last_error(void);
 

@@ -22,7 +22,8 @@ import numpy as np
 __all__ = [
     "SrkError", "SrkOpts", "SrkStats", "Graph",
     "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
-    "srk_multi_source", "srk_last_error", "library_path",
+    "srk_multi_source", "srk_single_source_noalloc", "srk_last_error",
+    "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
     "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_MAX_LEN",
     "SRK_MAX_WALKS",
@@ -31,6 +32,7 @@ __all__ = [
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
 SRK_DEVICE_PTRS, SRK_VALIDATE = 1, 2
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
+SRK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libsrk.so")
@@ -71,12 +73,13 @@ _lib.srk_graph_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32),
 _lib.srk_single_source.argtypes = [_vp, ctypes.c_int32, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_uint64,
                                    ctypes.POINTER(SrkOpts), _vp, _vp, _vp, _vp]
+_lib.srk_single_source_noalloc.argtypes = _lib.srk_single_source.argtypes
 _lib.srk_multi_source.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double,
                                   _vp, ctypes.c_uint64, ctypes.POINTER(SrkOpts),
                                   _vp, _vp, _vp]
 _lib.srk_last_error.restype = ctypes.c_char_p
 for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
-           "srk_single_source", "srk_multi_source"):
+           "srk_single_source", "srk_single_source_noalloc", "srk_multi_source"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -226,6 +229,26 @@ def srk_single_source(g: Graph, s: int, c: float, eps: float, seed: int,
     rc = _lib.srk_single_source(g.handle, int(s), float(c), float(eps),
                                 int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                                 sc, mc, ws, _stream_handle(stream))
+    del k1, k2, k3, k4
+    _check(rc)
+
+
+def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
+                              scores, meet_counts=None, weight_sums=None, *,
+                              z_override=None, L_override=None, p=None, q=None,
+                              step_counts=None, stats: Optional[SrkStats] = None,
+                              timing_events=None, stream=None) -> None:
+    """``srk_single_source`` for callers that must not allocate device memory
+    while querying: the scratch is a static device array of
+    ``SRK_NOALLOC_SCRATCH_BYTES``; outputs must be device tensors; calls that
+    overlap on the GPU race on the shared scratch."""
+    sc, _, k1 = _ptr(scores, "float64")
+    mc, _, k2 = _ptr(meet_counts, "uint32")
+    ws, _, k3 = _ptr(weight_sums, "uint64")
+    o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events)
+    rc = _lib.srk_single_source_noalloc(g.handle, int(s), float(c), float(eps),
+                                        int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
+                                        sc, mc, ws, _stream_handle(stream))
     del k1, k2, k3, k4
     _check(rc)
 

@@ -62,4 +62,32 @@ struct DeviceGuard {
 // SM count of the current device (cached per device).
 int sm_count(int device);
 
+// Scratch of one query, carved from one device block (srk_query.cu).
+struct Workspace {
+  int32_t *spos, *seff, *kdraw, *grp_cnt, *rank, *grp_off, *items, *first,
+      *succ, *sigma, *pair_j, *Hc, *small;
+  unsigned long long *pair_w;
+  size_t bytes;
+};
+
+// Device outputs of one query (null = not wanted, except scores).
+struct Outputs {
+  double *scores;
+  uint32_t *counts;
+  unsigned long long *wsums;
+  uint32_t *steps;
+};
+
+// Carves `base` (or only sizes the plan when base is null); returns the
+// number of bytes one query of table `t` needs.
+size_t plan(const QueryTab &t, Workspace *w, char *base);
+// Enqueues steps a2-a5 on `st`; `timing` (may be null) gets two events
+// recorded around the target-walk kernel.
+int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
+                  const Outputs &o, cudaStream_t st,
+                  const cudaEvent_t *timing = nullptr);
+// Copies the query counters into `stats` (synchronises `st`).
+int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
+               srk_stats *stats, bool accumulate);
+
 }  // namespace srk

@@ -1,0 +1,95 @@
+// srk_single_source_noalloc: the single-source query with its scratch taken
+// from a fixed, statically allocated device array instead of a memory pool.
+//
+// Who needs it: callers that must not allocate device memory while they issue
+// queries -- an application whose own caching allocator owns the whole device
+// budget, a serving thread that must not block on (or fail in) the driver's
+// allocator, or code running where allocation calls are off limits.  The graph
+// handle is created beforehand (srk_graph_load with SRK_DEVICE_PTRS borrows the
+// caller's arrays); after that this entry point calls no cudaMalloc, cudaFree,
+// cudaMallocAsync or any other allocating routine.
+//
+// The scratch is one file-scope __device__ array of SRK_NOALLOC_SCRATCH_BYTES.
+// It exists on every device on which this module is loaded, until the process
+// exits.  Its device address is looked up once per device with
+// cudaGetSymbolAddress, by the first call on that device (so that first call
+// should come before any stream capture).  All calls share the array and it
+// keeps the previous call's contents: every part a query needs zeroed is
+// cleared by the query itself, and calls whose work overlaps on the GPU (for
+// instance on two streams) race on it.
+#include <mutex>
+
+#include "srk_internal.h"
+
+// The scratch of every srk_single_source_noalloc call (see above).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SRK_NOALLOC_SCRATCH_BYTES];
+
+namespace srk {
+namespace {
+
+std::mutex g_addr_mu;
+void *g_addr[64] = {};
+
+// Device address of the scratch array on `device` (the current device).
+int scratch_address(int device, char **out) {
+  if (device < 0 || device >= 64) return fail(SRK_EINVAL, "device %d out of range", device);
+  std::lock_guard<std::mutex> lk(g_addr_mu);
+  if (!g_addr[device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                       "srk_single_source_noalloc: scratch address");
+    g_addr[device] = p;
+  }
+  *out = static_cast<char *>(g_addr[device]);
+  return SRK_OK;
+}
+
+}  // namespace
+}  // namespace srk
+
+using namespace srk;
+
+extern "C" int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c,
+                                         double eps, uint64_t seed,
+                                         const srk_opts *opt, double *scores,
+                                         uint32_t *meet_counts,
+                                         uint64_t *weight_sums,
+                                         void *cuda_stream) {
+  clear_error();
+  if (!g) return fail(SRK_EINVAL, "null graph");
+  if (!scores) return fail(SRK_EINVAL, "scores is null");
+  if (opt && opt->flags != 0) return fail(SRK_EINVAL, "opts.flags must be 0");
+  uint32_t *step_counts = opt ? opt->step_counts : nullptr;
+  QueryTab t;
+  int rc = build_table(g->n, s, c, eps, seed, opt, &t);
+  if (rc) return rc;
+  DeviceGuard guard(g->device);
+  // host outputs would need a device staging buffer: only device memory here
+  if (!is_device_ptr(scores) || (meet_counts && !is_device_ptr(meet_counts)) ||
+      (weight_sums && !is_device_ptr(weight_sums)) ||
+      (step_counts && !is_device_ptr(step_counts)))
+    return fail(SRK_EINVAL, "srk_single_source_noalloc takes device output pointers only");
+  Workspace w;
+  const size_t need = plan(t, &w, nullptr);
+  if (need > (size_t)SRK_NOALLOC_SCRATCH_BYTES)
+    return fail(SRK_EINVAL,
+                "query needs %zu bytes of scratch (N_tot = %d walks, L = %d); the "
+                "static scratch of srk_single_source_noalloc holds %zu bytes",
+                need, t.N_tot, t.L, (size_t)SRK_NOALLOC_SCRATCH_BYTES);
+  char *base = nullptr;
+  rc = scratch_address(g->device, &base);
+  if (rc) return rc;
+  plan(t, &w, base);
+  Outputs o;
+  o.scores = scores;
+  o.counts = meet_counts;
+  o.wsums = reinterpret_cast<unsigned long long *>(weight_sums);
+  o.steps = step_counts;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  rc = enqueue_query(g, t, w, o, st,
+                     opt ? (const cudaEvent_t *)opt->timing_events : nullptr);
+  if (!rc && opt && opt->stats) rc = read_stats(t, w, st, opt->stats, false);
+  return rc;
+}

@@ -380,14 +380,9 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-struct Workspace {
-  int32_t *spos, *seff, *kdraw, *grp_cnt, *rank, *grp_off, *items, *first,
-      *succ, *sigma, *pair_j, *Hc, *small;
-  unsigned long long *pair_w;
-  size_t bytes;
-};
 
-static size_t plan(const QueryTab &t, Workspace *w, char *base) {
+
+size_t plan(const QueryTab &t, Workspace *w, char *base) {
   const size_t N = (size_t)t.N_tot;
   const size_t Ls = (size_t)(t.L > 0 ? t.L : 1);
   size_t hc = 0;
@@ -435,18 +430,12 @@ static int target_grid(int device) {
   return sm_count(device) * b;
 }
 
-struct Outputs {
-  double *scores;
-  uint32_t *counts;
-  unsigned long long *wsums;
-  uint32_t *steps;
-};
+
 
 // Enqueues one query on `st` with device-resident outputs `o`.  Workspace
 // `w` (already carved) must hold plan(t) bytes.
-static int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
-                         const Outputs &o, cudaStream_t st,
-                         const cudaEvent_t *timing = nullptr) {
+int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
+                  const Outputs &o, cudaStream_t st, const cudaEvent_t *timing) {
   const int dev = g->device;
   const int N = t.N_tot;
   const int gN = grid_for(N, 256, dev);
@@ -489,8 +478,8 @@ static int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace 
 }
 
 // Reads back the counters of the small block into `stats` (synchronous).
-static int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
-                      srk_stats *stats, bool accumulate) {
+int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
+               srk_stats *stats, bool accumulate) {
   unsigned long long ctr[2] = {0, 0};
   int32_t active = 0;
   cudaError_t e = cudaMemcpyAsync(ctr, w.small + kSmallWords, sizeof ctr,
