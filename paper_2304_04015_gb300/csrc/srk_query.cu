@@ -283,13 +283,17 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
 }
 
 // -------------------------------------------------------------- steps a4-a5 --
-// One warp per target u at a time (grid-stride over targets), lanes over the
-// pairs a = lane, lane+32, ... of the cap-sorted list.  Pair a (original index
-// j) walks from u: step i draws from Philox counter ((i-1)>>1, j, u, s); the
-// walk meets when its node equals row i of the hit table, ends after cap
-// steps (a >= cnt[i+1]) or at a node without in-neighbours.  The first
-// meeting adds 1 to the count and the pair's weight to W_u; the warp then
-// reduces and writes count, W and s~(s,u) = W 2^-32 / z (s~(s,s) = 1).
+// Each warp takes targets u from a global counter.  Its 32 lanes walk the
+// target's pairs a = 0, 1, ... of the cap-sorted list; a lane whose walk ends
+// takes the next unassigned pair at once (lane refill), so early ends at
+// nodes without in-neighbours do not idle the warp.  Pair a (original index
+// j) walks from u: one Philox block, counter ((i-1)>>1, j, u, s), serves the
+// odd step i (words 0,1) and the even step i+1 (words 2,3).  A step moves to
+// I(x)[floor(R |I(x)| / 2^64)]; the walk meets when its node equals row i of
+// the hit table, ends after cap steps (a >= cnt[i+1]) or at a node without
+// in-neighbours.  The first meeting adds 1 to the count and the pair's weight
+// to W_u.  The warp then reduces and writes count, W and s~(s,u) = W 2^-32 / z
+// (s~(s,s) = 1).
 struct TargetArgs {
   const int32_t *row_ptr;
   const int32_t *col;
@@ -305,25 +309,25 @@ struct TargetArgs {
   unsigned long long *wsums;
   uint32_t *steps_per_target;
   unsigned long long *steps_total;
+  int32_t *target_counter;  // zeroed before the launch
 };
 
 __global__ void __launch_bounds__(256)
 k_target_walks(const __grid_constant__ TargetArgs A) {
-  __shared__ int32_t cnt[SRK_MAX_LEN + 2];
-  __shared__ int32_t R[SRK_MAX_LEN + 2];
+  __shared__ int32_t cnt[SRK_MAX_LEN + 3];
+  __shared__ int32_t R[SRK_MAX_LEN + 3];
   {
     const int32_t *cb = A.small_base + (SRK_MAX_LEN + 2);
     const int32_t *rb = A.small_base + 2 * (SRK_MAX_LEN + 2);
-    for (int i = threadIdx.x; i <= A.L + 1; i += blockDim.x) {
-      cnt[i] = cb[i];
-      R[i] = rb[i];
+    for (int i = threadIdx.x; i <= A.L + 2; i += blockDim.x) {
+      cnt[i] = (i <= A.L + 1) ? cb[i] : 0;  // cnt[L+1] = cnt[L+2] = 0
+      R[i] = (i <= A.L + 1) ? rb[i] : 0;
     }
   }
   __syncthreads();
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31;
-  const int32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t lanes_below = (1u << lane) - 1u;
   const int32_t n_pairs = cnt[1];
   const uint32_t s = (uint32_t)A.s;
   const int32_t *__restrict__ row_ptr = A.row_ptr;
@@ -331,31 +335,70 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
   const int32_t *__restrict__ Hc = A.Hc;
   const int32_t *__restrict__ pair_j = A.pair_j;
   unsigned long long warp_steps = 0;
-  for (int32_t u = warp; u < A.n; u += nwarps) {
+  for (;;) {
+    int32_t u = 0;
+    if (lane == 0) u = atomicAdd(A.target_counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= A.n) break;
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
-    if (u != A.s) {
-      const int32_t beg_u = row_ptr[u];
-      const int32_t deg_u = row_ptr[u + 1] - beg_u;
-      if (deg_u > 0) {
-        for (int32_t a = lane; a < n_pairs; a += 32) {
-          const uint32_t j = (uint32_t)pair_j[a];
-          int32_t beg = beg_u, deg = deg_u;
-          uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
-          for (int i = 1; i <= A.L; ++i) {
-            if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, j, (uint32_t)u, s, x0, x1, x2, x3);
-            const uint32_t hi = (i & 1) ? x0 : x2, lo = (i & 1) ? x1 : x3;
-            const int32_t x = col[beg + (int32_t)draw_index(hi, lo, (uint32_t)deg)];
-            ++st;
-            if (x == Hc[R[i] + a]) {
-              ++c;
-              W += A.pair_w[a];
-              break;
+    const int32_t beg_u = row_ptr[u];
+    const int32_t deg_u = row_ptr[u + 1] - beg_u;
+    if (u != A.s && deg_u > 0) {
+      int32_t next = 0;  // first unassigned pair (warp-uniform)
+      bool live = false;
+      int32_t a = 0, i = 1, beg = 0, deg = 0;
+      uint32_t j = 0;
+      for (;;) {
+        const uint32_t idle = __ballot_sync(0xffffffffu, !live);
+        if (idle) {
+          if (!live) {
+            a = next + __popc(idle & lanes_below);
+            if (a < n_pairs) {
+              live = true;
+              j = (uint32_t)pair_j[a];
+              i = 1;
+              beg = beg_u;
+              deg = deg_u;
             }
-            if (a >= cnt[i + 1]) break;  // cap reached
+          }
+          next += __popc(idle);
+        }
+        if (!__any_sync(0xffffffffu, live)) break;
+        if (live) {
+          uint32_t x0, x1, x2, x3;
+          philox(rk, (uint32_t)(i - 1) >> 1, j, (uint32_t)u, s, x0, x1, x2, x3);
+          // odd step i
+          int32_t x = col[beg + (int32_t)draw_index(x0, x1, (uint32_t)deg)];
+          ++st;
+          if (x == Hc[R[i] + a]) {
+            ++c;
+            W += A.pair_w[a];
+            live = false;
+          } else if (a >= cnt[i + 1]) {
+            live = false;  // cap reached
+          } else {
             beg = row_ptr[x];
             deg = row_ptr[x + 1] - beg;
-            if (deg == 0) break;  // no in-neighbours: the walk ends
+            if (deg == 0) {
+              live = false;  // no in-neighbours: the walk ends
+            } else {
+              // even step i+1
+              x = col[beg + (int32_t)draw_index(x2, x3, (uint32_t)deg)];
+              ++st;
+              if (x == Hc[R[i + 1] + a]) {
+                ++c;
+                W += A.pair_w[a];
+                live = false;
+              } else if (a >= cnt[i + 2]) {
+                live = false;
+              } else {
+                beg = row_ptr[x];
+                deg = row_ptr[x + 1] - beg;
+                if (deg == 0) live = false;
+                i += 2;
+              }
+            }
           }
         }
       }
@@ -469,6 +512,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.wsums = o.wsums;
   A.steps_per_target = o.steps;
   A.steps_total = reinterpret_cast<unsigned long long *>(w.small + kSmallWords);
+  A.target_counter = w.small + kSmallWords + 4;  // third 8-byte counter slot
   if (timing) cudaEventRecord(timing[0], st);
   k_target_walks<<<target_grid(dev), 256, 0, st>>>(A);
   if (timing) cudaEventRecord(timing[1], st);
