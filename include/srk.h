@@ -189,6 +189,19 @@ int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c,
                               double *scores, uint32_t *meet_counts,
                               uint64_t *weight_sums, void *cuda_stream);
 
+/*
+ * srk_probe_gather -- measurement utility (the paper has no counterpart): the
+ * random-gather roofline a walk step is measured against.  Enqueues one kernel
+ * on `cuda_stream` in which every thread of a full-occupancy grid performs
+ * `iters` rounds of four independent random 4-byte loads from `data` (device,
+ * n int32 entries, 1 <= n < 2^32), indices from per-thread linear congruential
+ * generators seeded by `seed`.  `sink` (device, one uint64) keeps the loads
+ * alive; `loads` (host, may be NULL) receives the number of loads issued.  The
+ * caller times the launch (e.g. with CUDA events) and divides.
+ */
+int srk_probe_gather(const int32_t *data, int64_t n, int64_t iters, uint32_t seed,
+                     unsigned long long *sink, int64_t *loads, void *cuda_stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char *srk_last_error(void);
 

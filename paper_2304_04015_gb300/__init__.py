@@ -22,7 +22,8 @@ import numpy as np
 __all__ = [
     "SrkError", "SrkOpts", "SrkStats", "Graph",
     "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
-    "srk_multi_source", "srk_single_source_noalloc", "srk_last_error",
+    "srk_multi_source", "srk_single_source_noalloc", "srk_probe_gather",
+    "srk_last_error",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
     "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_MAX_LEN",
@@ -77,9 +78,12 @@ _lib.srk_single_source_noalloc.argtypes = _lib.srk_single_source.argtypes
 _lib.srk_multi_source.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double,
                                   _vp, ctypes.c_uint64, ctypes.POINTER(SrkOpts),
                                   _vp, _vp, _vp]
+_lib.srk_probe_gather.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
+                                  _vp, ctypes.POINTER(ctypes.c_int64), _vp]
 _lib.srk_last_error.restype = ctypes.c_char_p
 for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
-           "srk_single_source", "srk_single_source_noalloc", "srk_multi_source"):
+           "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
+           "srk_probe_gather"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -270,3 +274,19 @@ def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
                                _stream_handle(stream))
     del k1, k2
     _check(rc)
+
+
+def srk_probe_gather(data, iters: int, seed: int, sink, stream=None) -> int:
+    """Enqueue the random-gather probe over ``data`` (device int32 tensor);
+    returns the number of 4-byte loads it issues.  ``sink``: device int64[1]."""
+    dp, d_dev, k1 = _ptr(data, "int32")
+    sp, s_dev, k2 = _ptr(sink, "uint64")
+    if not (d_dev and s_dev):
+        raise ValueError("data and sink must be device tensors")
+    n = data.numel()
+    loads = ctypes.c_int64()
+    rc = _lib.srk_probe_gather(dp, int(n), int(iters), int(seed) & 0xFFFFFFFF, sp,
+                               ctypes.byref(loads), _stream_handle(stream))
+    del k1, k2
+    _check(rc)
+    return loads.value

@@ -161,6 +161,39 @@ __global__ void k_validate_csr(const int32_t *__restrict__ row_ptr,
   }
 }
 
+// Packed adjacency (layout in srk_internal.h): node v's in-degree followed by
+// its in-neighbours' (degree code, position) entries, in the CSR's list
+// order, at pos(v) = v + row_ptr[v].  A walk step reads one entry, which
+// names the next node and usually its degree too, instead of a row_ptr pair
+// and a col entry.
+__global__ void k_build_adj_heads(const int32_t *__restrict__ row_ptr, int32_t n,
+                                  uint32_t *__restrict__ adj) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    adj[v + row_ptr[v]] = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+}
+
+// Edge e of list v (row_ptr[v] <= e < row_ptr[v+1]) lands at
+// pos(v) + 1 + (e - row_ptr[v]) = v + 1 + e.
+__global__ void k_build_adj_lists(const int32_t *__restrict__ row_ptr,
+                                  const int32_t *__restrict__ col, int32_t n,
+                                  int64_t m, int pos_bits,
+                                  uint32_t *__restrict__ adj) {
+  const uint32_t dmax = (uint32_t)((1ull << (32 - pos_bits)) - 1ull);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    int32_t lo = 0, hi = n - 1;  // last v with row_ptr[v] <= e
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo + 1) / 2;
+      if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int32_t y = col[e];
+    const uint32_t dy = (uint32_t)(row_ptr[y + 1] - row_ptr[y]);
+    const uint32_t code = dy < dmax ? dy : dmax;
+    adj[(int64_t)lo + 1 + e] = (code << pos_bits) | (uint32_t)(y + row_ptr[y]);
+  }
+}
+
 }  // namespace srk
 
 using namespace srk;
@@ -184,6 +217,7 @@ extern "C" int srk_graph_free(srk_graph *g) {
     if (g->own_row_ptr) cudaFree(g->own_row_ptr);
     if (g->own_col) cudaFree(g->own_col);
     if (g->own_w) cudaFree(g->own_w);
+    if (g->adj) cudaFree(g->adj);
   }
   delete g;
   return rc;
@@ -197,6 +231,8 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
   *out = nullptr;
   if (n < 1) return fail(SRK_EINVAL, "n = %d must be >= 1", n);
   if (m < 0 || m > INT32_MAX) return fail(SRK_EINVAL, "m = %lld outside [0, 2^31)", (long long)m);
+  if ((int64_t)n + m > INT32_MAX)
+    return fail(SRK_EINVAL, "n + m = %lld must stay below 2^31", (long long)n + (long long)m);
   if (!row_ptr || (m > 0 && !col)) return fail(SRK_EINVAL, "null CSR array");
   if (flags & ~(SRK_DEVICE_PTRS | SRK_VALIDATE))
     return fail(SRK_EINVAL, "unknown flags 0x%x", flags);
@@ -262,6 +298,26 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
       srk_graph_free(g);
       return fail(SRK_EINVAL, "malformed CSR: row_ptr must start at 0, end at m and "
                               "not decrease; col entries must lie in [0, n)");
+    }
+  }
+  {
+    int pb = 1;
+    while (pb < 31 && ((int64_t)1 << pb) < (int64_t)n + m) ++pb;  // positions < n + m
+    g->pos_bits = pb;
+    if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) * ((size_t)n + (size_t)m))) != cudaSuccess) {
+      int rc = cuda_fail(e, "srk_graph_load: packed adjacency");
+      srk_graph_free(g);
+      return rc;
+    }
+    k_build_adj_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, g->adj);
+    if (m > 0)
+      k_build_adj_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, pb, g->adj);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      int rc = cuda_fail(e, "srk_graph_load: building the packed adjacency");
+      srk_graph_free(g);
+      return rc;
     }
   }
   *out = g;

@@ -12,6 +12,15 @@ struct srk_graph {
   const int32_t *row_ptr = nullptr;  // device, n+1
   const int32_t *col = nullptr;      // device, m
   const float *edge_w = nullptr;     // device, m or null
+  // Packed adjacency (owned, n + m words): node v occupies the words
+  // pos(v) = v + row_ptr[v] .. pos(v) + |I(v)|.  adj[pos(v)] = |I(v)|; entry
+  // k of the list, adj[pos(v) + 1 + k], holds the k-th in-neighbour y as
+  // (min(|I(y)|, deg_max) << pos_bits) | pos(y), deg_max = 2^(32-pos_bits) - 1,
+  // so a walk step learns the next node's degree from the entry it reads and
+  // reads the header only when the degree is deg_max or more.  A node's
+  // position is its identity inside the walk kernels.
+  uint32_t *adj = nullptr;
+  int32_t pos_bits = 1;  // positions < 2^pos_bits
   int32_t *own_row_ptr = nullptr;    // owned copies (null when borrowed)
   int32_t *own_col = nullptr;
   float *own_w = nullptr;

@@ -50,11 +50,13 @@ __device__ __forceinline__ Small small_view(int32_t *base) {
 // Walk r of the source has length l = stratum(r).  Step i >= 1 draws 64 bits
 // from Philox counter ((i-1)>>1, r, s, s), word pair 2*((i-1)&1) (high, low),
 // and moves to I(x)[floor(R * |I(x)| / 2^64)]; it stops early at a node with
-// no in-neighbours.  The same thread computes Fisher-Yates draw t = r,
+// no in-neighbours.  Walks run on the packed adjacency (degree, then the
+// in-neighbours' positions), so nodes are identified by their position.  The same thread computes Fisher-Yates draw t = r,
 // k_t = floor(R * (t+1) / 2^64) with R from counter (t>>1, ~0, ~0, s).
 __global__ void __launch_bounds__(256)
 k_source_walks(const int32_t *__restrict__ row_ptr,
-               const int32_t *__restrict__ col, const __grid_constant__ QueryTab tab,
+               const uint32_t *__restrict__ adj, int pos_bits,
+               const __grid_constant__ QueryTab tab,
                int32_t *__restrict__ spos, int32_t *__restrict__ seff,
                int32_t *__restrict__ kdraw, int32_t *__restrict__ grp_cnt,
                int32_t *__restrict__ small_base) {
@@ -64,6 +66,10 @@ k_source_walks(const int32_t *__restrict__ row_ptr,
   const RoundKeys rk = round_keys(tab.key0, tab.key1);
   const int Ls = tab.L > 0 ? tab.L : 1;
   const uint32_t s = (uint32_t)tab.s;
+  const int32_t p_s = tab.s + row_ptr[tab.s];  // position of s in adj
+  const uint32_t pmask = (uint32_t)((1ull << pos_bits) - 1ull);
+  const uint32_t dmax = (uint32_t)((1ull << (32 - pos_bits)) - 1ull);
+  const uint32_t deg_s = adj[p_s];
   unsigned long long steps = 0;
   for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < tab.N_tot;
        r += gridDim.x * blockDim.x) {
@@ -77,17 +83,19 @@ k_source_walks(const int32_t *__restrict__ row_ptr,
       kdraw[0] = 0;
     }
     const int len = stratum_of(P, tab.L, r);
-    int32_t v = tab.s;
+    int32_t p = p_s;
+    uint32_t deg = deg_s;
     int eff = len;
     int32_t *out = spos + (int64_t)r * Ls;
     for (int i = 1; i <= len; ++i) {
-      const int32_t beg = row_ptr[v];
-      const int32_t deg = row_ptr[v + 1] - beg;
       if (deg == 0) { eff = i - 1; break; }
       if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
       const uint32_t hi = (i & 1) ? x0 : x2, lo = (i & 1) ? x1 : x3;
-      v = col[beg + (int32_t)draw_index(hi, lo, (uint32_t)deg)];
-      out[i - 1] = v;
+      const uint32_t e = adj[p + 1 + (int32_t)draw_index(hi, lo, deg)];
+      p = (int32_t)(e & pmask);
+      out[i - 1] = p;  // nodes are recorded by their position in adj
+      const uint32_t code = e >> pos_bits;
+      deg = code < dmax ? code : adj[p];
     }
     seff[r] = eff;
     steps += (unsigned long long)eff;
@@ -285,8 +293,11 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
 // -------------------------------------------------------------- steps a4-a5 --
 // Each warp takes targets u from a global counter.  Its 32 lanes walk the
 // target's pairs a = 0, 1, ... of the cap-sorted list; a lane whose walk ends
-// takes the next unassigned pair at once (lane refill), so early ends at
-// nodes without in-neighbours do not idle the warp.  Pair a (original index
+// takes the next unassigned pair at once (lane refill), so walks that end
+// early (cap, meeting, no in-neighbours) do not idle the warp.  Walks run on
+// the packed adjacency: from a node at position p with degree d, a step reads
+// entry adj[p + 1 + index], which holds the next node's position and, unless
+// that node's degree is large, its degree as well.  Pair a (original index
 // j) walks from u: one Philox block, counter ((i-1)>>1, j, u, s), serves the
 // odd step i (words 0,1) and the even step i+1 (words 2,3).  A step moves to
 // I(x)[floor(R |I(x)| / 2^64)]; the walk meets when its node equals row i of
@@ -295,8 +306,9 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
 // to W_u.  The warp then reduces and writes count, W and s~(s,u) = W 2^-32 / z
 // (s~(s,s) = 1).
 struct TargetArgs {
-  const int32_t *row_ptr;
-  const int32_t *col;
+  const int32_t *row_ptr;  // start positions of the targets: u + row_ptr[u]
+  const uint32_t *adj;     // packed adjacency (see srk_internal.h)
+  int32_t pos_bits;
   int32_t n, s, L;
   uint32_t key0, key1;
   double z;
@@ -312,7 +324,10 @@ struct TargetArgs {
   int32_t *target_counter;  // zeroed before the launch
 };
 
-__global__ void __launch_bounds__(256)
+// 8 blocks of 256 threads per SM (32 registers): the kernel is bound by the
+// rate of scattered L1 misses, and full occupancy keeps the most misses in
+// flight.
+__global__ void __launch_bounds__(256, 8)
 k_target_walks(const __grid_constant__ TargetArgs A) {
   __shared__ int32_t cnt[SRK_MAX_LEN + 3];
   __shared__ int32_t R[SRK_MAX_LEN + 3];
@@ -330,9 +345,11 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
   const uint32_t lanes_below = (1u << lane) - 1u;
   const int32_t n_pairs = cnt[1];
   const uint32_t s = (uint32_t)A.s;
-  const int32_t *__restrict__ row_ptr = A.row_ptr;
-  const int32_t *__restrict__ col = A.col;
+  const uint32_t *__restrict__ adj = A.adj;
   const int32_t *__restrict__ Hc = A.Hc;
+  const int pb = A.pos_bits;
+  const uint32_t pmask = (uint32_t)((1ull << pb) - 1ull);
+  const uint32_t dmax = (uint32_t)((1ull << (32 - pb)) - 1ull);
   const int32_t *__restrict__ pair_j = A.pair_j;
   unsigned long long warp_steps = 0;
   for (;;) {
@@ -342,8 +359,8 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
     if (u >= A.n) break;
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
-    const int32_t beg_u = row_ptr[u];
-    const int32_t deg_u = row_ptr[u + 1] - beg_u;
+    const int32_t beg_u = u + A.row_ptr[u];  // position of u
+    const int32_t deg_u = (int32_t)adj[beg_u];
     if (u != A.s && deg_u > 0) {
       int32_t next = 0;  // first unassigned pair (warp-uniform)
       bool live = false;
@@ -369,7 +386,8 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
           uint32_t x0, x1, x2, x3;
           philox(rk, (uint32_t)(i - 1) >> 1, j, (uint32_t)u, s, x0, x1, x2, x3);
           // odd step i
-          int32_t x = col[beg + (int32_t)draw_index(x0, x1, (uint32_t)deg)];
+          uint32_t e = adj[beg + 1 + (int32_t)draw_index(x0, x1, (uint32_t)deg)];
+          int32_t x = (int32_t)(e & pmask);
           ++st;
           if (x == Hc[R[i] + a]) {
             ++c;
@@ -378,13 +396,15 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
           } else if (a >= cnt[i + 1]) {
             live = false;  // cap reached
           } else {
-            beg = row_ptr[x];
-            deg = row_ptr[x + 1] - beg;
+            beg = x;
+            const uint32_t code = e >> pb;
+            deg = (int32_t)(code < dmax ? code : adj[x]);
             if (deg == 0) {
               live = false;  // no in-neighbours: the walk ends
             } else {
               // even step i+1
-              x = col[beg + (int32_t)draw_index(x2, x3, (uint32_t)deg)];
+              e = adj[beg + 1 + (int32_t)draw_index(x2, x3, (uint32_t)deg)];
+              x = (int32_t)(e & pmask);
               ++st;
               if (x == Hc[R[i + 1] + a]) {
                 ++c;
@@ -393,8 +413,9 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
               } else if (a >= cnt[i + 2]) {
                 live = false;
               } else {
-                beg = row_ptr[x];
-                deg = row_ptr[x + 1] - beg;
+                beg = x;
+                const uint32_t code2 = e >> pb;
+                deg = (int32_t)(code2 < dmax ? code2 : adj[x]);
                 if (deg == 0) live = false;
                 i += 2;
               }
@@ -484,7 +505,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   const int gN = grid_for(N, 256, dev);
   cudaError_t e = cudaMemsetAsync(w.small, 0, 4 * kSmallWords + 64, st);
   if (e != cudaSuccess) return cuda_fail(e, "clearing query counters");
-  k_source_walks<<<gN, 256, 0, st>>>(g->row_ptr, g->col, t, w.spos, w.seff,
+  k_source_walks<<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos, w.seff,
                                      w.kdraw, w.grp_cnt, w.small);
   k_fy_rank<<<gN, 256, 0, st>>>(w.kdraw, w.grp_cnt, w.rank, N);
   k_scan<<<1, 1024, 0, st>>>(w.grp_cnt, w.grp_off, N);
@@ -496,7 +517,8 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
                                   w.pair_w, w.Hc);
   TargetArgs A;
   A.row_ptr = g->row_ptr;
-  A.col = g->col;
+  A.adj = g->adj;
+  A.pos_bits = g->pos_bits;
   A.n = g->n;
   A.s = t.s;
   A.L = t.L;
