@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="approximate CPU time budget of the oracle baseline")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-probe", action="store_true")
     return ap.parse_args()
 
 
@@ -141,6 +142,44 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gather_probe(srk, torch, dev, n_words):
+    """Random 4-byte gather rate (loads/s) on an n_words int32 array."""
+    data = torch.randint(0, 1 << 30, (n_words,), dtype=torch.int32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    srk.srk_probe_gather(data, 64, 1, sink)
+    torch.cuda.synchronize()
+    iters, rate = 500, 0.0
+    for rep in range(3):
+        ev[0].record()
+        loads = srk.srk_probe_gather(data, iters, 11 + rep, sink)
+        ev[1].record()
+        ev[1].synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        rate = max(rate, loads / t) if rep else rate
+        if rep == 0:
+            iters = max(100, int(iters * 0.05 / t))
+    del data
+    return rate
+
+
+def recorded_traffic():
+    """DRAM bytes per target-walk step of the target-walk kernel, from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_target_walks_rmat20_traffic.json")) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, "paper_2304_04015_gb300", "csrc", "srk_query.cu")
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("srk_query_cu_sha256") != sha:
+            return None
+        return float(rec["dram_bytes_per_launch"]) / float(rec["target_steps_of_launch"])
+    except Exception:
+        return None
 
 
 def cpu_baseline(rp, col, sources, budget_s):
@@ -318,13 +357,26 @@ def main():
 
     peak, peak_kind = load_peaks()
     kern_s = float(np.sum(k_ms)) / 1e3
+    target_steps_per_s = tgt_steps / kern_s
     achieved = tgt_steps * BYTES_PER_STEP / kern_s / 1e9
+    per_step = recorded_traffic()
+    traffic = per_step * tgt_steps / args.steps if per_step is not None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_target_walks", "peak_kind": peak_kind,
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_target_walks", "peak_kind": peak_kind + " (HBM copy)",
                 "bytes_per_unit": BYTES_PER_STEP, "unit_name": "target-walk step",
                 "kernel_ms_per_launch": float(np.mean(k_ms)),
                 "kernel_share_of_query": float(np.sum(k_ms) / np.sum(q_ms))}
+    gather = None
+    if not args.skip_probe:
+        l2_rate = gather_probe(srk, torch, dev, n + m)          # graph-sized array
+        hbm_rate = gather_probe(srk, torch, dev, 1 << 30)       # 4 GB array
+        gather = {"probe_gathers_per_s_graph_sized": l2_rate,
+                  "probe_gathers_per_s_4GB": hbm_rate,
+                  "kernel_steps_per_s": target_steps_per_s,
+                  "frac_of_graph_sized_probe": target_steps_per_s / l2_rate,
+                  "note": "one scattered 4-byte adjacency read per target-walk step; "
+                          "probe = srk_probe_gather, independent random loads at full occupancy"}
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -345,7 +397,8 @@ def main():
                        "parallelism": "sources sharded over ranks" if world > 1 else "1 GPU"},
             "walk_steps_per_s": steps_per_s,
             "target_steps_per_query": tgt_steps / args.steps,
-            "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
+            "e2e": e2e, "clocks": clk,
             "gpu_launches": 9 * args.steps,
             "wall_s_timed_loop": t_wall, "graph_gen_s": t_gen}
     if rank == 0:
