@@ -70,6 +70,22 @@ def dist_env():
     return rank, world, local
 
 
+def shard_sources(sources, rank: int, world: int):
+    """Sources of this rank: queries are independent, so ranks take disjoint
+    strided slices and exchange nothing but timings (weak scaling)."""
+    return sources[rank::world] if world > 1 else sources
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    """The slowest rank's time (all_reduce MAX); identity on one rank."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload():
     from srk_inputs import rmat_in_csr, uniform_sources
     rp, col = rmat_in_csr(SCALE, seed=GRAPH_SEED)
@@ -268,7 +284,7 @@ def main():
     rp, col, sources = make_workload()
     t_gen = time.perf_counter() - t_gen
     n, m = rp.size - 1, col.size
-    my_sources = sources[rank::world] if world > 1 else sources
+    my_sources = shard_sources(sources, rank, world)
 
     rp_d = torch.from_numpy(rp).to(dev)
     col_d = torch.from_numpy(col).to(dev)
@@ -321,11 +337,7 @@ def main():
         pg.barrier()
     clk = clocks.stop()
 
-    total_ms = float(np.sum(q_ms))
-    if pg:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(float(np.sum(q_ms)), pg, dev)
     queries = args.steps * world
     value = queries / (total_ms / 1e3)
     tgt_steps = sum(x[0] for x in stats_steps)
@@ -344,10 +356,7 @@ def main():
             t0 = time.perf_counter()
             query(i, host_scores.numpy())     # D2H copy + sync inside the call
             e2e_s += time.perf_counter() - t0
-        if pg:
-            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(e2e_s, pg, dev)
         e2e = {"value": queries / e2e_s, "unit": "queries/s",
                "h2d_bytes_per_step": 3108,
                "d2h_bytes_per_step": 8 * n,
