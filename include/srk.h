@@ -54,6 +54,10 @@ extern "C" {
 #define SRK_ETIMEOUT (-4)  /* a bounded device wait gave up */
 #define SRK_ENOTSUP  (-5)  /* the request is valid but not supported */
 
+/* srk_opts.flags */
+#define SRK_OPT_NO_GRAPH 1  /* srk_multi_source: enqueue launches directly
+                               instead of through a captured CUDA graph */
+
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */
 #define SRK_VALIDATE    2  /* accepted; the CSR invariants are always checked */
@@ -82,7 +86,7 @@ typedef struct srk_opts {
                               eps is then not used */
     int32_t  L_override;   /* >= 0: truncation length instead of
                               floor(p ln n / ln(1/sqrt(c))); < 0: paper */
-    int32_t  flags;        /* reserved, 0 */
+    int32_t  flags;        /* 0, or SRK_OPT_NO_GRAPH (srk_multi_source only) */
     double   p;            /* threshold knob of Appendix B.5, >= 1 (0 means 1) */
     double   q;            /* failure knob of Appendix B.5, >= 1 (0 means 1) */
     uint32_t *step_counts; /* NULL or n entries (host or device memory):
@@ -149,14 +153,25 @@ int srk_single_source(const srk_graph *g, int32_t s, double c, double eps,
                       void *cuda_stream);
 
 /*
- * srk_multi_source -- k independent single-source queries.
+ * srk_multi_source -- k independent single-source queries, batched.
  *   sources : k source nodes (host memory).
- *   eps     : k error targets (host memory), one per source.
- *   scores  : k x n FP64 outputs, row i for sources[i].
+ *   eps     : k error targets (host memory), one per source, so the sources'
+ *             walk budgets N_tot differ.
+ *   scores  : k x n FP64 outputs (host or device), row i for sources[i].
  *   meet_counts : NULL or k x n uint32 outputs.
- * Query i uses the same seed; its walks differ because the source is part of
- * every Philox counter.  Results equal k calls of srk_single_source.
- * opt->step_counts must be NULL here; opt->stats, if set, receives totals.
+ * Results equal k calls of srk_single_source with the same seed (each walk's
+ * Philox counter contains its source).  The sources run in batches sized by
+ * a scratch budget (a quarter of free device memory, at most 8 GiB, or the
+ * byte count in the environment variable SRK_BATCH_BYTES): one
+ * launch per source-side phase for the whole batch, then one persistent
+ * launch over the batch's (source, target) work items, captured in a CUDA
+ * graph unless opt->flags has SRK_OPT_NO_GRAPH.  Sources none of whose walk
+ * pairs can meet (e.g. no in-neighbours) and targets without in-neighbours
+ * produce no work items; their scores are written directly.  The persistent
+ * kernel's launch shape is picked per graph by timing the candidate shapes on
+ * the first items of the first call (kept in the handle).  The call
+ * synchronises the stream at the end of every batch.  opt->step_counts must
+ * be NULL; opt->stats, if set, receives totals over all sources.
  */
 int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
                      double c, const double *eps, uint64_t seed,

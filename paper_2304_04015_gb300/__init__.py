@@ -26,12 +26,13 @@ __all__ = [
     "srk_last_error",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
-    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_MAX_LEN",
+    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_OPT_NO_GRAPH", "SRK_MAX_LEN",
     "SRK_MAX_WALKS",
 ]
 
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
 SRK_DEVICE_PTRS, SRK_VALIDATE = 1, 2
+SRK_OPT_NO_GRAPH = 1
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
 SRK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -197,11 +198,11 @@ def srk_graph_info(g: Graph):
 
 
 def _opts(z_override=None, L_override=None, p=None, q=None, step_counts=None,
-          stats: Optional[SrkStats] = None, timing_events=None):
+          stats: Optional[SrkStats] = None, timing_events=None, flags: int = 0):
     o = SrkOpts()
     o.z_override = float(z_override) if z_override else 0.0
     o.L_override = int(L_override) if L_override is not None else -1
-    o.flags = 0
+    o.flags = int(flags)
     o.p = float(p) if p else 0.0
     o.q = float(q) if q else 0.0
     sp, _, keep = _ptr(step_counts, "uint32")
@@ -260,15 +261,17 @@ def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
 def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
                      meet_counts=None, *, z_override=None, L_override=None,
                      p=None, q=None, stats: Optional[SrkStats] = None,
-                     stream=None) -> None:
+                     no_graph: bool = False, stream=None) -> None:
     """k queries (``srk_multi_source``): ``sources`` and ``eps`` are host
-    sequences of length k; ``scores`` is k x n float64."""
+    sequences of length k; ``scores`` is k x n float64.  ``no_graph``: enqueue
+    the batch launches directly instead of through a captured CUDA graph."""
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
     k = src.size
     eps_a = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (k,)))
     sc, _, k1 = _ptr(scores, "float64")
     mc, _, k2 = _ptr(meet_counts, "uint32")
-    o, _ = _opts(z_override, L_override, p, q, None, stats)
+    o, _ = _opts(z_override, L_override, p, q, None, stats,
+                 flags=SRK_OPT_NO_GRAPH if no_graph else 0)
     rc = _lib.srk_multi_source(g.handle, src.ctypes.data, k, float(c), eps_a.ctypes.data,
                                int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), sc, mc,
                                _stream_handle(stream))

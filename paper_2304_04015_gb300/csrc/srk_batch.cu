@@ -1,0 +1,601 @@
+// srk_multi_source: many single-source queries with uneven walk budgets.
+//
+// The sources are processed in batches sized by a memory budget.  Each batch
+// runs the source-side steps a2-a3 of all its sources with one launch per
+// phase (thread g of a phase finds its source by a binary search over the
+// prefix of the sources' walk counts), then one persistent launch walks every
+// (source, target) work item: a warp takes items from a global counter in
+// source-major order and walks the target's pairs exactly as the
+// single-source kernel does (walk_target in srk_device.cuh), so the results
+// are identical to srk_single_source.  Sources whose walks never leave the
+// source (no pair can meet) are short-circuited: their score rows are
+// prefilled (1 at the source, 0 elsewhere) and they contribute no items, and
+// neither do targets without in-neighbours.  A batch's launches are captured
+// in a CUDA graph and launched as one.  The persistent kernel's launch shape
+// (block size x blocks per SM) is chosen per graph by timing the candidates
+// on the first items of the first batch (autotuner).
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "srk_device.cuh"
+#include "srk_internal.h"
+
+namespace srk {
+
+// One source of a batch, as the batched kernels see it (device memory).
+struct BatchSrc {
+  Workspace w;            // the source's scratch (see plan())
+  const QueryTab *tab;    // the source's table (device copy)
+  double *scores;         // output row, n entries
+  uint32_t *counts;       // output row or null
+  unsigned long long *steps;  // target-walk steps of this source (one counter)
+  int32_t s, L, N_tot;
+  double z;
+};
+
+struct BatchArgs {
+  const BatchSrc *src;
+  const int64_t *walk_off;  // prefix of N_tot over the batch, k+1 entries
+  int32_t k;
+  int64_t total_walks;
+  const int32_t *row_ptr;
+  const uint32_t *adj;
+  int32_t pos_bits;
+  uint32_t key0, key1;
+};
+
+__device__ __forceinline__ int find_source(const int64_t *off, int k, int64_t g) {
+  int lo = 0, hi = k - 1;  // last i with off[i] <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+#define SRK_BATCH_LOOP(A, ...)                                                   \
+  for (int64_t g_ = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;              \
+       g_ < (A).total_walks; g_ += (int64_t)gridDim.x * blockDim.x) {            \
+    const int i_ = find_source((A).walk_off, (A).k, g_);                         \
+    const BatchSrc &S_ = (A).src[i_];                                            \
+    const int32_t r_ = (int32_t)(g_ - (A).walk_off[i_]);                         \
+    __VA_ARGS__                                                                  \
+  }
+
+// a2: source walks and Fisher-Yates draws of every source of the batch.
+__global__ void __launch_bounds__(256) kb_source_walks(const __grid_constant__ BatchArgs A) {
+  const RoundKeys rk = round_keys(A.key0, A.key1);
+  const Adj G = make_adj(A.adj, A.pos_bits);
+  SRK_BATCH_LOOP(A, {
+    const QueryTab &t = *S_.tab;
+    const uint32_t s = (uint32_t)S_.s;
+    const int32_t p_s = S_.s + A.row_ptr[S_.s];
+    const int Ls = S_.L > 0 ? S_.L : 1;
+    S_.w.grp_cnt[r_] = 0;
+    S_.w.kdraw[r_] = (r_ >= 1) ? fy_draw(rk, s, r_) : 0;
+    const int len = stratum_of(t.P, S_.L, r_);
+    const int eff = source_walk(rk, G, s, p_s, G.adj[p_s], r_, len,
+                                S_.w.spos + (int64_t)r_ * Ls);
+    S_.w.seff[r_] = eff;
+    atomicAdd(small_view(S_.w.small).ctr + 1, (unsigned long long)eff);
+  })
+}
+
+__global__ void kb_fy_rank(const __grid_constant__ BatchArgs A) {
+  SRK_BATCH_LOOP(A, {
+    if (r_ >= 1) S_.w.rank[r_] = atomicAdd(&S_.w.grp_cnt[S_.w.kdraw[r_]], 1);
+  })
+}
+
+// Exclusive scan of each source's group counts: block b scans source b.
+__global__ void __launch_bounds__(1024) kb_scan(const __grid_constant__ BatchArgs A) {
+  __shared__ int32_t warp_sum[32];
+  __shared__ int32_t carry;
+  const BatchSrc &S = A.src[blockIdx.x];
+  const int32_t N = S.N_tot;
+  const int32_t *cnt = S.w.grp_cnt;
+  int32_t *off = S.w.grp_off;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < N; base += 4096) {
+    const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+    int32_t v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (i0 + q < N) ? cnt[i0 + q] : 0;
+    const int32_t local = v[0] + v[1] + v[2] + v[3];
+    int32_t incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t ws = warp_sum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sum[lane] = ws;
+    }
+    __syncthreads();
+    int32_t run = carry + (wid ? warp_sum[wid - 1] : 0) + incl - local;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (i0 + q < N) off[i0 + q] = run;
+      run += v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = run;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[N] = carry;
+}
+
+__global__ void kb_fy_scatter(const __grid_constant__ BatchArgs A) {
+  SRK_BATCH_LOOP(A, {
+    if (r_ >= 1) S_.w.items[S_.w.grp_off[S_.w.kdraw[r_]] + S_.w.rank[r_]] = r_;
+  })
+}
+
+__global__ void kb_fy_groups(const __grid_constant__ BatchArgs A) {
+  SRK_BATCH_LOOP(A, {
+    const int32_t b = S_.w.grp_off[r_], e = S_.w.grp_off[r_ + 1];
+    int32_t *items = S_.w.items;
+    for (int32_t x = b + 1; x < e; ++x) {  // insertion sort (groups are tiny)
+      const int32_t y = items[x];
+      int32_t q = x - 1;
+      while (q >= b && items[q] > y) { items[q + 1] = items[q]; --q; }
+      items[q + 1] = y;
+    }
+    S_.w.first[r_] = (e > b) ? items[b] : -1;
+    for (int32_t x = b; x < e; ++x) S_.w.succ[items[x]] = (x + 1 < e) ? items[x + 1] : -1;
+  })
+}
+
+__global__ void kb_pairs(const __grid_constant__ BatchArgs A) {
+  SRK_BATCH_LOOP(A, {
+    const int32_t p = resolve_sigma(r_, S_.w.kdraw, S_.w.first, S_.w.succ, S_.N_tot);
+    S_.w.sigma[r_] = p;
+    const int32_t cap = min(stratum_of(S_.tab->P, S_.L, r_), S_.w.seff[p]);
+    if (cap >= 1) atomicAdd(&small_view(S_.w.small).cap_hist[cap], 1);
+  })
+}
+
+// Row geometry of every source (one thread per source), as in k_rows, and
+// the list of sources with at least one pair.
+__global__ void kb_rows(const __grid_constant__ BatchArgs A, int32_t *act_src,
+                        int32_t *n_act_src) {
+  if (blockIdx.x != 0) return;
+  for (int i = threadIdx.x; i < A.k; i += blockDim.x) {
+    const Small sm = small_view(A.src[i].w.small);
+    const int L = A.src[i].L;
+    int32_t c = 0;
+    sm.cnt[L + 1] = 0;
+    for (int q = L; q >= 1; --q) {
+      sm.cursor[q] = c;
+      c += sm.cap_hist[q];
+      sm.cnt[q] = c;
+    }
+    int32_t r = 0;
+    for (int q = 1; q <= L + 1; ++q) {
+      sm.R[q] = r;
+      if (q <= L) r += sm.cnt[q];
+    }
+    sm.cnt[0] = c;
+    sm.R[0] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // in source order, so the items stay source-major
+    int32_t m = 0;
+    for (int i = 0; i < A.k; ++i)
+      if (small_view(A.src[i].w.small).cnt[1] > 0) act_src[m++] = i;
+    *n_act_src = m;
+  }
+}
+
+__global__ void kb_hit_table(const __grid_constant__ BatchArgs A) {
+  SRK_BATCH_LOOP(A, {
+    const int32_t j = r_;
+    const int32_t w = S_.w.sigma[j];
+    const int l2 = stratum_of(S_.tab->P, S_.L, j);
+    const int32_t cap = min(l2, S_.w.seff[w]);
+    if (cap >= 1) {
+      const Small sm = small_view(S_.w.small);
+      const int l1 = stratum_of(S_.tab->P, S_.L, w);
+      const int32_t a = atomicAdd(&sm.cursor[cap], 1);
+      S_.w.pair_j[a] = j;
+      S_.w.pair_w[a] = __double2ull_rn(S_.tab->a[l1] * S_.tab->a[l2] * 4294967296.0);
+      const int Ls = S_.L > 0 ? S_.L : 1;
+      const int32_t *sp = S_.w.spos + (int64_t)w * Ls;
+      for (int q = 1; q <= cap; ++q) S_.w.Hc[sm.R[q] + a] = sp[q - 1];
+    }
+  })
+}
+
+// Every output row: 1 at the source, 0 elsewhere (the rows of items walked
+// later are overwritten per target).
+__global__ void kb_prefill(const BatchSrc *__restrict__ src, int32_t k, int32_t n) {
+  const int64_t total = (int64_t)k * n;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(g / n);
+    const int32_t u = (int32_t)(g - (int64_t)i * n);
+    src[i].scores[u] = (u == src[i].s) ? 1.0 : 0.0;
+    if (src[i].counts) src[i].counts[u] = 0;
+  }
+}
+
+// a4-a5 for every (active source, target with in-neighbours) item, source-
+// major.  Items at or beyond `item_limit` are not walked (autotuner trials).
+// Each warp keeps its current source's context in shared memory: the pair
+// list pointers and the rows cnt[0..L+2], R[0..L+2] (dynamic shared memory,
+// 2 (Lmax + 3) words per warp), so the walk loop holds no per-source state
+// in registers.
+template <int kBlock, int kMinBlocks>
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
+                int32_t n_act, const int32_t *__restrict__ act_src,
+                const int32_t *__restrict__ n_act_src_p,
+                unsigned long long *__restrict__ item_counter, int64_t item_limit,
+                int32_t row_words) {
+  extern __shared__ int32_t rows[];
+  __shared__ PairSet ctx[kBlock / 32];
+  const RoundKeys rk = round_keys(A.key0, A.key1);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t lanes_below = (1u << lane) - 1u;
+  const Adj G = make_adj(A.adj, A.pos_bits);
+  int32_t *my_cnt = rows + (2 * wib) * row_words;
+  int32_t *my_R = my_cnt + row_words;
+  const int64_t n_items = (int64_t)(*n_act_src_p) * n_act;
+  const int64_t limit = item_limit < n_items ? item_limit : n_items;
+  int cur = -1;
+  unsigned long long acc = 0;  // steps of source `cur` by this warp (lane 0)
+  for (;;) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(item_counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if ((int64_t)item >= limit) break;
+    const int q = (int)((int64_t)item / n_act);
+    const int32_t u = act[(int64_t)item - (int64_t)q * n_act];
+    const int i = act_src[q];
+    if (i != cur) {
+      if (lane == 0 && cur >= 0 && acc) atomicAdd(A.src[cur].steps, acc);
+      acc = 0;
+      cur = i;
+      const BatchSrc &B = A.src[i];
+      const Small sm = small_view(B.w.small);
+      __syncwarp();
+      for (int x = lane; x <= B.L + 2; x += 32) {
+        my_cnt[x] = (x <= B.L + 1) ? sm.cnt[x] : 0;
+        my_R[x] = (x <= B.L + 1) ? sm.R[x] : 0;
+      }
+      if (lane == 0) {
+        PairSet &S = ctx[wib];
+        S.cnt = my_cnt;
+        S.R = my_R;
+        S.pair_j = B.w.pair_j;
+        S.pair_w = B.w.pair_w;
+        S.Hc = B.w.Hc;
+        S.n_pairs = sm.cnt[1];
+        S.s = (uint32_t)B.s;
+      }
+      __syncwarp();
+    }
+    if (u == A.src[i].s) continue;  // prefilled with 1
+    uint32_t c = 0, st = 0;
+    unsigned long long W = 0;
+    const int32_t beg_u = u + A.row_ptr[u];
+    walk_target(rk, G, ctx[wib], (uint32_t)u, beg_u, G.adj[beg_u], lanes_below, c, W, st);
+    for (int off = 16; off > 0; off >>= 1) {
+      c += __shfl_xor_sync(0xffffffffu, c, off);
+      st += __shfl_xor_sync(0xffffffffu, st, off);
+      W += __shfl_xor_sync(0xffffffffu, W, off);
+    }
+    if (lane == 0) {
+      const BatchSrc &B = A.src[i];
+      B.scores[u] = (double)W * 2.3283064365386963e-10 / B.z;
+      if (B.counts) B.counts[u] = c;
+      acc += st;
+    }
+  }
+  if (lane == 0 && cur >= 0 && acc) atomicAdd(A.src[cur].steps, acc);
+}
+
+// The candidate launch shapes of the autotuner (block size, blocks per SM).
+struct Shape {
+  int block, per_sm;
+};
+static const Shape kShapes[] = {{256, 8}, {512, 4}, {128, 16}, {1024, 2}, {256, 6}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+static void launch_targets(int shape, int sms, cudaStream_t st, const BatchArgs &A,
+                           const int32_t *act, int32_t n_act, const int32_t *act_src,
+                           const int32_t *n_act_src, unsigned long long *ctr,
+                           int64_t limit, int Lmax) {
+  const Shape sh = kShapes[shape];
+  const int grid = sms * sh.per_sm;
+  const int32_t rw = Lmax + 3;
+  const size_t smem = sizeof(int32_t) * 2 * (size_t)rw * (size_t)(sh.block / 32);
+  switch (shape) {
+    case 0: kb_target_walks<256, 8><<<grid, 256, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 1: kb_target_walks<512, 4><<<grid, 512, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 2: kb_target_walks<128, 16><<<grid, 128, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 3: kb_target_walks<1024, 2><<<grid, 1024, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    default: kb_target_walks<256, 6><<<grid, 256, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+  }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static std::mutex g_stream_mu;
+static cudaStream_t g_cap_stream[64] = {};
+
+// A library-owned non-blocking stream per device for graph capture (the
+// caller's stream may be the legacy default stream, which cannot capture).
+static cudaStream_t capture_stream(int dev) {
+  std::lock_guard<std::mutex> lk(g_stream_mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!g_cap_stream[dev]) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    g_cap_stream[dev] = s;
+  }
+  return g_cap_stream[dev];
+}
+
+}  // namespace srk
+
+using namespace srk;
+
+extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
+                                int32_t k, double c, const double *eps,
+                                uint64_t seed, const srk_opts *opt,
+                                double *scores, uint32_t *meet_counts,
+                                void *cuda_stream) {
+  clear_error();
+  if (!g) return fail(SRK_EINVAL, "null graph");
+  if (k < 0) return fail(SRK_EINVAL, "k = %d is negative", k);
+  if (k == 0) return SRK_OK;
+  if (!sources || !eps || !scores) return fail(SRK_EINVAL, "null argument");
+  if (opt && opt->step_counts)
+    return fail(SRK_EINVAL, "step_counts is not supported by srk_multi_source");
+  if (opt && (opt->flags & ~SRK_OPT_NO_GRAPH))
+    return fail(SRK_EINVAL, "unknown opts.flags 0x%x", opt->flags);
+  const bool use_graph = !(opt && (opt->flags & SRK_OPT_NO_GRAPH));
+  const size_t n = (size_t)g->n;
+  // a1 for every source (host, FP64)
+  std::vector<QueryTab> tabs((size_t)k);
+  for (int32_t i = 0; i < k; ++i) {
+    int rc = build_table(g->n, sources[i], c, eps[i], seed, opt, &tabs[i]);
+    if (rc) return fail(rc, "source %d (index %d): %s", sources[i], i, srk_last_error());
+  }
+  DeviceGuard guard(g->device);
+  const int dev = g->device;
+  const int sms = sm_count(dev);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool d_scores = is_device_ptr(scores);
+  const bool d_counts = !meet_counts || is_device_ptr(meet_counts);
+  cudaMemPool_t mp = pool(dev);
+  if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
+  cudaStream_t cs = use_graph ? capture_stream(dev) : st;
+  if (use_graph && !cs) return fail(SRK_ECUDA, "cannot create the capture stream");
+
+  // batch shape: as many sources as fit a scratch budget
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  size_t budget = std::max<size_t>((size_t)256 << 20,
+                                   std::min<size_t>((size_t)8 << 30, free_b / 4));
+  if (const char *env = getenv("SRK_BATCH_BYTES")) {  // explicit scratch budget
+    const unsigned long long v = strtoull(env, nullptr, 10);
+    if (v > 0) budget = (size_t)v;
+  }
+  srk_stats total;
+  memset(&total, 0, sizeof total);
+  int32_t i0 = 0;
+  int rc = SRK_OK;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  if (use_graph) {
+    cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
+  }
+  while (i0 < k && rc == SRK_OK) {
+    // sources [i0, i1) form this batch
+    size_t need = 0;
+    int32_t i1 = i0;
+    std::vector<size_t> ws_off;
+    while (i1 < k) {
+      Workspace w;
+      const size_t b = align256(plan(tabs[i1], &w, nullptr)) +
+                       (d_scores ? 0 : align256(8 * n)) + (d_counts ? 0 : align256(4 * n));
+      if (i1 > i0 && need + b > budget) break;
+      ws_off.push_back(need);
+      need += b;
+      ++i1;
+    }
+    const int32_t kb = i1 - i0;
+    int Lmax = 0;
+    for (int32_t b = i0; b < i1; ++b) Lmax = std::max(Lmax, tabs[(size_t)b].L);
+    const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
+                        align256(sizeof(int64_t) * (kb + 1)) + align256(sizeof(int32_t) * (kb + 1)) +
+                        align256(sizeof(unsigned long long) * (kb + 1));
+    char *base = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&base, head + need, mp, st);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "batch workspace allocation"); break; }
+    BatchSrc *d_src = (BatchSrc *)base;
+    QueryTab *d_tab = (QueryTab *)(base + align256(sizeof(BatchSrc) * kb));
+    int64_t *d_off = (int64_t *)((char *)d_tab + align256(sizeof(QueryTab) * kb));
+    int32_t *d_act_src = (int32_t *)((char *)d_off + align256(sizeof(int64_t) * (kb + 1)));
+    unsigned long long *d_ctr = (unsigned long long *)((char *)d_act_src +
+                                                         align256(sizeof(int32_t) * (kb + 1)));
+    // d_ctr[0] = item counter, d_ctr[1 + i] = steps of source i; n_act_src in d_act_src[kb]
+    char *ws_base = base + head;
+    std::vector<BatchSrc> hsrc((size_t)kb);
+    std::vector<int64_t> hoff((size_t)kb + 1);
+    hoff[0] = 0;
+    for (int32_t b = 0; b < kb; ++b) {
+      const QueryTab &t = tabs[(size_t)(i0 + b)];
+      BatchSrc &S = hsrc[(size_t)b];
+      char *wb = ws_base + ws_off[(size_t)b];
+      const size_t core = align256(plan(t, &S.w, wb));
+      char *extra = wb + core;
+      S.tab = d_tab + b;
+      S.scores = d_scores ? scores + (size_t)(i0 + b) * n : (double *)extra;
+      if (!d_scores) extra += align256(8 * n);
+      S.counts = !meet_counts ? nullptr
+                 : (d_counts ? meet_counts + (size_t)(i0 + b) * n : (uint32_t *)extra);
+      S.steps = d_ctr + 1 + b;
+      S.s = t.s;
+      S.L = t.L;
+      S.N_tot = t.N_tot;
+      S.z = t.z;
+      hoff[(size_t)b + 1] = hoff[(size_t)b] + t.N_tot;
+    }
+    // tables and source descriptors (synchronous staging of pageable memory)
+    if ((e = cudaMemcpyAsync(d_tab, tabs.data() + i0, sizeof(QueryTab) * kb,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_src, hsrc.data(), sizeof(BatchSrc) * kb,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_off, hoff.data(), sizeof(int64_t) * (kb + 1),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+      rc = cuda_fail(e, "batch descriptors");
+      cudaFreeAsync(base, st);
+      break;
+    }
+    BatchArgs A;
+    A.src = d_src;
+    A.walk_off = d_off;
+    A.k = kb;
+    A.total_walks = hoff[(size_t)kb];
+    A.row_ptr = g->row_ptr;
+    A.adj = g->adj;
+    A.pos_bits = g->pos_bits;
+    A.key0 = (uint32_t)seed;
+    A.key1 = (uint32_t)(seed >> 32);
+    const int gw = (int)std::max<int64_t>(1, std::min<int64_t>((A.total_walks + 255) / 256,
+                                                                (int64_t)sms * 8));
+    auto enqueue_source_side = [&](cudaStream_t s2) {
+      for (int32_t b = 0; b < kb; ++b)
+        cudaMemsetAsync(hsrc[(size_t)b].w.small, 0, kSmallBytes, s2);
+      cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * (kb + 1), s2);
+      kb_source_walks<<<gw, 256, 0, s2>>>(A);
+      kb_fy_rank<<<gw, 256, 0, s2>>>(A);
+      kb_scan<<<kb, 1024, 0, s2>>>(A);
+      kb_fy_scatter<<<gw, 256, 0, s2>>>(A);
+      kb_fy_groups<<<gw, 256, 0, s2>>>(A);
+      kb_pairs<<<gw, 256, 0, s2>>>(A);
+      kb_rows<<<1, 256, 0, s2>>>(A, d_act_src, d_act_src + kb);
+      kb_hit_table<<<gw, 256, 0, s2>>>(A);
+      const int gp = (int)std::min<int64_t>(((int64_t)kb * (int64_t)n + 255) / 256,
+                                            (int64_t)sms * 16);
+      kb_prefill<<<gp, 256, 0, s2>>>(d_src, kb, (int32_t)n);
+    };
+    // autotune the persistent kernel's launch shape on the first batch
+    int shape = g->batch_cfg;
+    if (shape < 0 || shape >= kNumShapes) {
+      enqueue_source_side(st);
+      cudaEvent_t t0, t1;
+      cudaEventCreate(&t0);
+      cudaEventCreate(&t1);
+      const int64_t trial = (int64_t)sms * 64 * 3;  // about three items per warp
+      float best = 1e30f;
+      shape = 0;
+      for (int sh = 0; sh < kNumShapes; ++sh) {
+        cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
+        cudaEventRecord(t0, st);
+        launch_targets(sh, sms, st, A, g->act, g->n_act, d_act_src, d_act_src + kb, d_ctr, trial,
+                       Lmax);
+        cudaEventRecord(t1, st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(t1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms < best) {
+          best = ms;
+          shape = sh;
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      const_cast<srk_graph *>(g)->batch_cfg = shape;
+    }
+    auto enqueue_all = [&](cudaStream_t s2) {
+      enqueue_source_side(s2);
+      launch_targets(shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb, d_ctr,
+                     INT64_MAX, Lmax);
+    };
+    if (use_graph) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaEventRecord(ev_in, st);
+      cudaStreamWaitEvent(cs, ev_in, 0);
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        enqueue_all(cs);
+        e = cudaStreamEndCapture(cs, &graph);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+      if (e == cudaSuccess) e = cudaEventRecord(ev_out, cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_out, 0);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+    } else {
+      enqueue_all(st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "batched query launch");
+      cudaFreeAsync(base, st);
+      break;
+    }
+    // results of host callers
+    for (int32_t b = 0; b < kb && e == cudaSuccess; ++b) {
+      const BatchSrc &S = hsrc[(size_t)b];
+      if (!d_scores)
+        e = cudaMemcpyAsync(scores + (size_t)(i0 + b) * n, S.scores, 8 * n,
+                            cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess && meet_counts && !d_counts)
+        e = cudaMemcpyAsync(meet_counts + (size_t)(i0 + b) * n, S.counts, 4 * n,
+                            cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess && opt && opt->stats) {
+      std::vector<unsigned long long> steps((size_t)kb + 1);
+      e = cudaMemcpyAsync(steps.data(), d_ctr, sizeof(unsigned long long) * (kb + 1),
+                          cudaMemcpyDeviceToHost, st);
+      for (int32_t b = 0; b < kb && e == cudaSuccess; ++b) {
+        unsigned long long sc[2];
+        int32_t act = 0;
+        const Small sm = small_view(hsrc[(size_t)b].w.small);
+        e = cudaMemcpyAsync(sc, sm.ctr, sizeof sc, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(&act, sm.cnt + 1, sizeof act, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        total.source_steps += sc[1];
+        total.n_active_pairs += act;
+        total.n_walks += tabs[(size_t)(i0 + b)].N_tot;
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      for (int32_t b = 0; b < kb; ++b) total.target_steps += steps[(size_t)b + 1];
+      total.z = tabs[(size_t)(i1 - 1)].z;
+      total.L = tabs[(size_t)(i1 - 1)].L;
+    }
+    cudaFreeAsync(base, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "batched query results");
+    i0 = i1;
+  }
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (rc == SRK_OK && (!d_scores || !d_counts)) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "srk_multi_source");
+  }
+  if (rc == SRK_OK && opt && opt->stats) *opt->stats = total;
+  return rc;
+}

@@ -72,3 +72,200 @@ __device__ __forceinline__ int stratum_of(const int32_t *P, int L, int32_t r) {
 }
 
 }  // namespace srk
+
+// ------------------------------------------------------------------------
+// Shared pieces of the query kernels (single-source and batched paths).
+// ------------------------------------------------------------------------
+#include "srk.h"
+
+namespace srk {
+
+// Control block of one query (int32 words): cap histogram, row sizes cnt[i]
+// (pairs with cap >= i), hit-table row offsets R[i], per-cap cursors, then
+// four uint64 counters: [0] target steps, [1] source steps, [2] target/item
+// counter, [3] spare.
+constexpr int kRowWords = SRK_MAX_LEN + 2;
+constexpr int kSmallWords = 4 * kRowWords;
+constexpr int kSmallBytes = 4 * kSmallWords + 32;
+
+struct Small {
+  int32_t *cap_hist;
+  int32_t *cnt;
+  int32_t *R;
+  int32_t *cursor;
+  unsigned long long *ctr;
+};
+
+__host__ __device__ __forceinline__ Small small_view(int32_t *base) {
+  Small s;
+  s.cap_hist = base;
+  s.cnt = base + kRowWords;
+  s.R = base + 2 * kRowWords;
+  s.cursor = base + 3 * kRowWords;
+  s.ctr = reinterpret_cast<unsigned long long *>(base + kSmallWords);
+  return s;
+}
+
+// The packed adjacency: a node at position p has degree adj[p]; entry k of
+// its list, adj[p + 1 + k], is (degree code << pb) | position of the k-th
+// in-neighbour, the code being the degree when it is below dmax.
+struct Adj {
+  const uint32_t *adj;
+  int pb;
+  uint32_t pmask, dmax;
+};
+
+__host__ __device__ __forceinline__ Adj make_adj(const uint32_t *adj, int pb) {
+  Adj a;
+  a.adj = adj;
+  a.pb = pb;
+  a.pmask = (uint32_t)((1ull << pb) - 1ull);
+  a.dmax = (uint32_t)((1ull << (32 - pb)) - 1ull);
+  return a;
+}
+
+// The entry a step from the node at position p (degree deg > 0) reads with
+// the 64-bit draw (hi, lo): the in-neighbour of index floor(R deg / 2^64).
+__device__ __forceinline__ uint32_t adj_entry(const Adj &G, int32_t p, uint32_t deg,
+                                              uint32_t hi, uint32_t lo) {
+  return G.adj[p + 1 + (int32_t)draw_index(hi, lo, deg)];
+}
+__device__ __forceinline__ int32_t entry_pos(const Adj &G, uint32_t e) {
+  return (int32_t)(e & G.pmask);
+}
+// Degree of the node x = entry_pos(e): from the entry, or from x's header
+// when the degree does not fit the entry's code.
+__device__ __forceinline__ uint32_t entry_deg(const Adj &G, uint32_t e, int32_t x) {
+  const uint32_t code = e >> G.pb;
+  return code < G.dmax ? code : G.adj[x];
+}
+
+// Source walk r of length len from the node at position p_s (degree deg_s):
+// writes the position at step i to out[i-1]; returns the steps taken.  Step
+// i draws from Philox counter ((i-1)>>1, r, s, s), words 2((i-1)&1), +1.
+__device__ __forceinline__ int source_walk(const RoundKeys &rk, const Adj &G,
+                                           uint32_t s, int32_t p_s, uint32_t deg_s,
+                                           int32_t r, int len, int32_t *out) {
+  int32_t p = p_s;
+  uint32_t deg = deg_s;
+  uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+  for (int i = 1; i <= len; ++i) {
+    if (deg == 0) return i - 1;
+    if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
+    const uint32_t e = adj_entry(G, p, deg, (i & 1) ? x0 : x2, (i & 1) ? x1 : x3);
+    p = entry_pos(G, e);
+    out[i - 1] = p;
+    deg = entry_deg(G, e, p);
+  }
+  return len;
+}
+
+// Fisher-Yates draw t >= 1 of source s: k_t = floor(R (t+1) / 2^64), R from
+// counter (t>>1, ~0, ~0, s), words 2(t&1), +1.
+__device__ __forceinline__ int32_t fy_draw(const RoundKeys &rk, uint32_t s, int32_t t) {
+  uint32_t x0, x1, x2, x3;
+  philox(rk, (uint32_t)t >> 1, 0xFFFFFFFFu, 0xFFFFFFFFu, s, x0, x1, x2, x3);
+  return (int32_t)draw_index((t & 1) ? x2 : x0, (t & 1) ? x3 : x1, (uint32_t)t + 1u);
+}
+
+// sigma[j] of the sequential Fisher-Yates loop, from the draws and the
+// "next write of a position" links (see k_pairs in srk_query.cu).
+__device__ __forceinline__ int32_t resolve_sigma(int32_t j, const int32_t *kdraw,
+                                                 const int32_t *first,
+                                                 const int32_t *succ, int32_t N) {
+  int32_t p, h;
+  if (j == 0) {
+    p = 0;
+    h = first[0];
+  } else {
+    p = kdraw[j];
+    h = succ[j];
+  }
+  for (int32_t guard = 0; h >= 0 && guard < N; ++guard) {
+    p = h;
+    const int32_t f = first[p];
+    h = (f == p) ? succ[p] : f;
+  }
+  return p;
+}
+
+// One source's pairs as the target walks see them.
+struct PairSet {
+  const int32_t *cnt;  // cnt[i] = pairs with cap >= i, cnt[L+1] = 0
+  const int32_t *R;    // hit-table row offsets
+  const int32_t *pair_j;
+  const unsigned long long *pair_w;
+  const int32_t *Hc;
+  int32_t n_pairs;     // cnt[1]
+  uint32_t s;          // source id (Philox counter word 3)
+};
+
+// All pairs of target u (position beg_u, degree deg_u > 0) walked by one
+// warp with lane refill; per-lane totals of meetings c, weight W and steps st
+// are added to the arguments (not reduced across the warp).
+__device__ __forceinline__ void walk_target(const RoundKeys &rk, const Adj &G,
+                                            const PairSet &S, uint32_t u,
+                                            int32_t beg_u, uint32_t deg_u,
+                                            uint32_t lanes_below, uint32_t &c,
+                                            unsigned long long &W, uint32_t &st) {
+  int32_t next = 0;  // first unassigned pair (warp-uniform)
+  bool live = false;
+  int32_t a = 0, i = 1, p = 0;
+  uint32_t deg = 0, j = 0;
+  for (;;) {
+    const uint32_t idle = __ballot_sync(0xffffffffu, !live);
+    if (idle) {
+      if (!live) {
+        a = next + __popc(idle & lanes_below);
+        if (a < S.n_pairs) {
+          live = true;
+          j = (uint32_t)S.pair_j[a];
+          i = 1;
+          p = beg_u;
+          deg = deg_u;
+        }
+      }
+      next += __popc(idle);
+    }
+    if (!__any_sync(0xffffffffu, live)) break;
+    if (live) {
+      uint32_t x0, x1, x2, x3;
+      philox(rk, (uint32_t)(i - 1) >> 1, j, u, S.s, x0, x1, x2, x3);
+      // odd step i
+      uint32_t e = adj_entry(G, p, deg, x0, x1);
+      int32_t x = entry_pos(G, e);
+      ++st;
+      if (x == S.Hc[S.R[i] + a]) {
+        ++c;
+        W += S.pair_w[a];
+        live = false;
+      } else if (a >= S.cnt[i + 1]) {
+        live = false;  // cap reached
+      } else {
+        deg = entry_deg(G, e, x);
+        if (deg == 0) {
+          live = false;  // no in-neighbours: the walk ends
+        } else {
+          // even step i+1
+          e = adj_entry(G, x, deg, x2, x3);
+          x = entry_pos(G, e);
+          ++st;
+          if (x == S.Hc[S.R[i + 1] + a]) {
+            ++c;
+            W += S.pair_w[a];
+            live = false;
+          } else if (a >= S.cnt[i + 2]) {
+            live = false;
+          } else {
+            deg = entry_deg(G, e, x);
+            if (deg == 0) live = false;
+            p = x;
+            i += 2;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace srk

@@ -194,6 +194,21 @@ __global__ void k_build_adj_lists(const int32_t *__restrict__ row_ptr,
   }
 }
 
+__global__ void k_active_flags(const int32_t *__restrict__ row_ptr, int32_t n,
+                               int32_t *__restrict__ flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    flag[v] = row_ptr[v + 1] > row_ptr[v] ? 1 : 0;
+}
+
+__global__ void k_active_scatter(const int32_t *__restrict__ flag,
+                                 const int32_t *__restrict__ off, int32_t n,
+                                 int32_t *__restrict__ act) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    if (flag[v]) act[off[v]] = (int32_t)v;
+}
+
 }  // namespace srk
 
 using namespace srk;
@@ -218,6 +233,7 @@ extern "C" int srk_graph_free(srk_graph *g) {
     if (g->own_col) cudaFree(g->own_col);
     if (g->own_w) cudaFree(g->own_w);
     if (g->adj) cudaFree(g->adj);
+    if (g->act) cudaFree(g->act);
   }
   delete g;
   return rc;
@@ -319,6 +335,35 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
       srk_graph_free(g);
       return rc;
     }
+  }
+  {  // ascending list of the nodes with in-neighbours
+    int32_t *flag = nullptr, *off = nullptr;
+    if ((e = cudaMalloc(&flag, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+        (e = cudaMalloc(&off, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) {
+      if (flag) cudaFree(flag);
+      int rc = cuda_fail(e, "srk_graph_load: active-node list");
+      srk_graph_free(g);
+      return rc;
+    }
+    k_active_flags<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, flag);
+    k_scan<<<1, 1024>>>(flag, off, n);
+    int32_t n_act = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpy(&n_act, off + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && (e = cudaMalloc(&g->act, sizeof(int32_t) * (size_t)(n_act > 0 ? n_act : 1))) == cudaSuccess) {
+      k_active_scatter<<<sm_count(dev) * 4, 256>>>(flag, off, n, g->act);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(flag);
+    cudaFree(off);
+    if (e != cudaSuccess) {
+      int rc = cuda_fail(e, "srk_graph_load: active-node list");
+      srk_graph_free(g);
+      return rc;
+    }
+    g->n_act = n_act;
   }
   *out = g;
   return SRK_OK;

@@ -21,6 +21,13 @@ struct srk_graph {
   // position is its identity inside the walk kernels.
   uint32_t *adj = nullptr;
   int32_t pos_bits = 1;  // positions < 2^pos_bits
+  // Nodes with at least one in-neighbour, ascending (owned): the only targets
+  // whose score can be nonzero.
+  int32_t *act = nullptr;
+  int32_t n_act = 0;
+  // Launch shape of the batched target kernel chosen by the autotuner
+  // (-1: not tuned yet).
+  int batch_cfg = -1;
   int32_t *own_row_ptr = nullptr;    // owned copies (null when borrowed)
   int32_t *own_col = nullptr;
   float *own_w = nullptr;
@@ -95,6 +102,10 @@ size_t plan(const QueryTab &t, Workspace *w, char *base);
 int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
                   const Outputs &o, cudaStream_t st,
                   const cudaEvent_t *timing = nullptr);
+// Exclusive scan of cnt[0..N) into off[0..N] (one block of 1024 threads).
+__global__ void k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off,
+                       int32_t N);
+
 // Copies the query counters into `stats` (synchronises `st`).
 int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
                srk_stats *stats, bool accumulate);

@@ -24,28 +24,6 @@
 
 namespace srk {
 
-constexpr int kSmallWords = 4 * (SRK_MAX_LEN + 2);  // cap_hist, cnt, R, cursor
-
-// Layout of the small control block (int32 words), followed by 4 uint64
-// counters: [0] target steps, [1] source steps.
-struct Small {
-  int32_t *cap_hist;  // pairs per cap value 1..L
-  int32_t *cnt;       // cnt[i] = pairs with cap >= i (i = 1..L+1)
-  int32_t *R;         // R[i] = start of hit-table row i
-  int32_t *cursor;    // next free slot of each cap group
-  unsigned long long *ctr;
-};
-
-__device__ __forceinline__ Small small_view(int32_t *base) {
-  Small s;
-  s.cap_hist = base;
-  s.cnt = base + (SRK_MAX_LEN + 2);
-  s.R = base + 2 * (SRK_MAX_LEN + 2);
-  s.cursor = base + 3 * (SRK_MAX_LEN + 2);
-  s.ctr = reinterpret_cast<unsigned long long *>(base + kSmallWords);
-  return s;
-}
-
 // ---------------------------------------------------------------- step a2 --
 // Walk r of the source has length l = stratum(r).  Step i >= 1 draws 64 bits
 // from Philox counter ((i-1)>>1, r, s, s), word pair 2*((i-1)&1) (high, low),
@@ -67,36 +45,15 @@ k_source_walks(const int32_t *__restrict__ row_ptr,
   const int Ls = tab.L > 0 ? tab.L : 1;
   const uint32_t s = (uint32_t)tab.s;
   const int32_t p_s = tab.s + row_ptr[tab.s];  // position of s in adj
-  const uint32_t pmask = (uint32_t)((1ull << pos_bits) - 1ull);
-  const uint32_t dmax = (uint32_t)((1ull << (32 - pos_bits)) - 1ull);
+  const Adj G = make_adj(adj, pos_bits);
   const uint32_t deg_s = adj[p_s];
   unsigned long long steps = 0;
   for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < tab.N_tot;
        r += gridDim.x * blockDim.x) {
     grp_cnt[r] = 0;
-    uint32_t x0, x1, x2, x3;
-    if (r >= 1) {
-      philox(rk, (uint32_t)r >> 1, 0xFFFFFFFFu, 0xFFFFFFFFu, s, x0, x1, x2, x3);
-      const uint32_t hi = (r & 1) ? x2 : x0, lo = (r & 1) ? x3 : x1;
-      kdraw[r] = (int32_t)draw_index(hi, lo, (uint32_t)r + 1u);
-    } else {
-      kdraw[0] = 0;
-    }
+    kdraw[r] = (r >= 1) ? fy_draw(rk, s, r) : 0;
     const int len = stratum_of(P, tab.L, r);
-    int32_t p = p_s;
-    uint32_t deg = deg_s;
-    int eff = len;
-    int32_t *out = spos + (int64_t)r * Ls;
-    for (int i = 1; i <= len; ++i) {
-      if (deg == 0) { eff = i - 1; break; }
-      if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
-      const uint32_t hi = (i & 1) ? x0 : x2, lo = (i & 1) ? x1 : x3;
-      const uint32_t e = adj[p + 1 + (int32_t)draw_index(hi, lo, deg)];
-      p = (int32_t)(e & pmask);
-      out[i - 1] = p;  // nodes are recorded by their position in adj
-      const uint32_t code = e >> pos_bits;
-      deg = code < dmax ? code : adj[p];
-    }
+    const int eff = source_walk(rk, G, s, p_s, deg_s, r, len, spos + (int64_t)r * Ls);
     seff[r] = eff;
     steps += (unsigned long long)eff;
   }
@@ -213,19 +170,7 @@ k_pairs(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ kdraw,
   const int32_t N = tab.N_tot;
   for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < N;
        j += gridDim.x * blockDim.x) {
-    int32_t p, h;
-    if (j == 0) {
-      p = 0;
-      h = first[0];
-    } else {
-      p = kdraw[j];
-      h = succ[j];
-    }
-    for (int32_t guard = 0; h >= 0 && guard < N; ++guard) {
-      p = h;
-      const int32_t f = first[p];
-      h = (f == p) ? succ[p] : f;  // next write of position p after step p
-    }
+    const int32_t p = resolve_sigma(j, kdraw, first, succ, N);
     sigma[j] = p;
     const int l2 = stratum_of(P, tab.L, j);
     const int32_t cap = min(l2, seff[p]);
@@ -332,25 +277,25 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
   __shared__ int32_t cnt[SRK_MAX_LEN + 3];
   __shared__ int32_t R[SRK_MAX_LEN + 3];
   {
-    const int32_t *cb = A.small_base + (SRK_MAX_LEN + 2);
-    const int32_t *rb = A.small_base + 2 * (SRK_MAX_LEN + 2);
+    const Small sm = small_view(const_cast<int32_t *>(A.small_base));
     for (int i = threadIdx.x; i <= A.L + 2; i += blockDim.x) {
-      cnt[i] = (i <= A.L + 1) ? cb[i] : 0;  // cnt[L+1] = cnt[L+2] = 0
-      R[i] = (i <= A.L + 1) ? rb[i] : 0;
+      cnt[i] = (i <= A.L + 1) ? sm.cnt[i] : 0;  // cnt[L+1] = cnt[L+2] = 0
+      R[i] = (i <= A.L + 1) ? sm.R[i] : 0;
     }
   }
   __syncthreads();
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const int32_t n_pairs = cnt[1];
-  const uint32_t s = (uint32_t)A.s;
-  const uint32_t *__restrict__ adj = A.adj;
-  const int32_t *__restrict__ Hc = A.Hc;
-  const int pb = A.pos_bits;
-  const uint32_t pmask = (uint32_t)((1ull << pb) - 1ull);
-  const uint32_t dmax = (uint32_t)((1ull << (32 - pb)) - 1ull);
-  const int32_t *__restrict__ pair_j = A.pair_j;
+  const Adj G = make_adj(A.adj, A.pos_bits);
+  PairSet S;
+  S.cnt = cnt;
+  S.R = R;
+  S.pair_j = A.pair_j;
+  S.pair_w = A.pair_w;
+  S.Hc = A.Hc;
+  S.n_pairs = cnt[1];
+  S.s = (uint32_t)A.s;
   unsigned long long warp_steps = 0;
   for (;;) {
     int32_t u = 0;
@@ -360,70 +305,9 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
     const int32_t beg_u = u + A.row_ptr[u];  // position of u
-    const int32_t deg_u = (int32_t)adj[beg_u];
-    if (u != A.s && deg_u > 0) {
-      int32_t next = 0;  // first unassigned pair (warp-uniform)
-      bool live = false;
-      int32_t a = 0, i = 1, beg = 0, deg = 0;
-      uint32_t j = 0;
-      for (;;) {
-        const uint32_t idle = __ballot_sync(0xffffffffu, !live);
-        if (idle) {
-          if (!live) {
-            a = next + __popc(idle & lanes_below);
-            if (a < n_pairs) {
-              live = true;
-              j = (uint32_t)pair_j[a];
-              i = 1;
-              beg = beg_u;
-              deg = deg_u;
-            }
-          }
-          next += __popc(idle);
-        }
-        if (!__any_sync(0xffffffffu, live)) break;
-        if (live) {
-          uint32_t x0, x1, x2, x3;
-          philox(rk, (uint32_t)(i - 1) >> 1, j, (uint32_t)u, s, x0, x1, x2, x3);
-          // odd step i
-          uint32_t e = adj[beg + 1 + (int32_t)draw_index(x0, x1, (uint32_t)deg)];
-          int32_t x = (int32_t)(e & pmask);
-          ++st;
-          if (x == Hc[R[i] + a]) {
-            ++c;
-            W += A.pair_w[a];
-            live = false;
-          } else if (a >= cnt[i + 1]) {
-            live = false;  // cap reached
-          } else {
-            beg = x;
-            const uint32_t code = e >> pb;
-            deg = (int32_t)(code < dmax ? code : adj[x]);
-            if (deg == 0) {
-              live = false;  // no in-neighbours: the walk ends
-            } else {
-              // even step i+1
-              e = adj[beg + 1 + (int32_t)draw_index(x2, x3, (uint32_t)deg)];
-              x = (int32_t)(e & pmask);
-              ++st;
-              if (x == Hc[R[i + 1] + a]) {
-                ++c;
-                W += A.pair_w[a];
-                live = false;
-              } else if (a >= cnt[i + 2]) {
-                live = false;
-              } else {
-                beg = x;
-                const uint32_t code2 = e >> pb;
-                deg = (int32_t)(code2 < dmax ? code2 : adj[x]);
-                if (deg == 0) live = false;
-                i += 2;
-              }
-            }
-          }
-        }
-      }
-    }
+    const uint32_t deg_u = G.adj[beg_u];
+    if (u != A.s && deg_u > 0)
+      walk_target(rk, G, S, (uint32_t)u, beg_u, deg_u, lanes_below, c, W, st);
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
       st += __shfl_xor_sync(0xffffffffu, st, off);
@@ -471,7 +355,7 @@ size_t plan(const QueryTab &t, Workspace *w, char *base) {
   w->pair_j = (int32_t *)take(4 * N);
   w->pair_w = (unsigned long long *)take(8 * N);
   w->Hc = (int32_t *)take(4 * hc);
-  w->small = (int32_t *)take(4 * kSmallWords + 64);
+  w->small = (int32_t *)take(kSmallBytes);
   w->bytes = off;
   return off;
 }
@@ -503,7 +387,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   const int dev = g->device;
   const int N = t.N_tot;
   const int gN = grid_for(N, 256, dev);
-  cudaError_t e = cudaMemsetAsync(w.small, 0, 4 * kSmallWords + 64, st);
+  cudaError_t e = cudaMemsetAsync(w.small, 0, kSmallBytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "clearing query counters");
   k_source_walks<<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos, w.seff,
                                      w.kdraw, w.grp_cnt, w.small);
@@ -533,8 +417,8 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.counts = o.counts;
   A.wsums = o.wsums;
   A.steps_per_target = o.steps;
-  A.steps_total = reinterpret_cast<unsigned long long *>(w.small + kSmallWords);
-  A.target_counter = w.small + kSmallWords + 4;  // third 8-byte counter slot
+  A.steps_total = small_view(w.small).ctr;
+  A.target_counter = reinterpret_cast<int32_t *>(small_view(w.small).ctr + 2);
   if (timing) cudaEventRecord(timing[0], st);
   k_target_walks<<<target_grid(dev), 256, 0, st>>>(A);
   if (timing) cudaEventRecord(timing[1], st);
@@ -548,10 +432,10 @@ int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
                srk_stats *stats, bool accumulate) {
   unsigned long long ctr[2] = {0, 0};
   int32_t active = 0;
-  cudaError_t e = cudaMemcpyAsync(ctr, w.small + kSmallWords, sizeof ctr,
+  cudaError_t e = cudaMemcpyAsync(ctr, small_view(w.small).ctr, sizeof ctr,
                                   cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&active, w.small + (SRK_MAX_LEN + 2) + 1, sizeof active,
+    e = cudaMemcpyAsync(&active, small_view(w.small).cnt + 1, sizeof active,
                         cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reading query statistics");
@@ -632,44 +516,4 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
     if (e != cudaSuccess) rc = cuda_fail(e, "srk_single_source");
   }
   return rc;
-}
-
-extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
-                                int32_t k, double c, const double *eps,
-                                uint64_t seed, const srk_opts *opt,
-                                double *scores, uint32_t *meet_counts,
-                                void *cuda_stream) {
-  clear_error();
-  if (!g) return fail(SRK_EINVAL, "null graph");
-  if (k < 0) return fail(SRK_EINVAL, "k = %d is negative", k);
-  if (k == 0) return SRK_OK;
-  if (!sources || !eps || !scores) return fail(SRK_EINVAL, "null argument");
-  if (opt && opt->step_counts)
-    return fail(SRK_EINVAL, "step_counts is not supported by srk_multi_source");
-  srk_opts local;
-  memset(&local, 0, sizeof local);
-  local.L_override = -1;
-  if (opt) local = *opt;
-  srk_stats total;
-  memset(&total, 0, sizeof total);
-  const size_t n = (size_t)g->n;
-  for (int32_t i = 0; i < k; ++i) {
-    srk_stats one;
-    local.stats = (opt && opt->stats) ? &one : nullptr;
-    int rc = srk_single_source(g, sources[i], c, eps[i], seed, &local,
-                               scores + (size_t)i * n,
-                               meet_counts ? meet_counts + (size_t)i * n : nullptr,
-                               nullptr, cuda_stream);
-    if (rc) return fail(rc, "source %d (index %d): %s", sources[i], i, srk_last_error());
-    if (opt && opt->stats) {
-      total.z = one.z;
-      total.L = one.L;
-      total.n_walks += one.n_walks;
-      total.n_active_pairs += one.n_active_pairs;
-      total.source_steps += one.source_steps;
-      total.target_steps += one.target_steps;
-    }
-  }
-  if (opt && opt->stats) *opt->stats = total;
-  return SRK_OK;
 }

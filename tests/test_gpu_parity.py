@@ -258,3 +258,62 @@ def test_invalid_arguments_are_rejected(srk):
     bad_rp[10], bad_rp[11] = bad_rp[11] + 1, bad_rp[10]
     with pytest.raises(srk.SrkError):
         srk.srk_graph_load(bad_rp, col)
+
+
+def _multi(srk, rp, col, sources, eps, seed, device_out=True, no_graph=False, **kw):
+    import torch
+    dev = torch.device("cuda:0")
+    n = rp.size - 1
+    k = len(sources)
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        stats = srk.SrkStats()
+        if device_out:
+            sc = torch.empty((k, n), dtype=torch.float64, device=dev)
+            mc = torch.empty((k, n), dtype=torch.int32, device=dev)
+            srk.srk_multi_source(g, sources, C, eps, seed, sc, mc, stats=stats,
+                                 no_graph=no_graph, **kw)
+            torch.cuda.synchronize()
+            return sc.cpu().numpy(), mc.cpu().numpy().view(np.uint32), stats
+        sc = np.empty((k, n), dtype=np.float64)
+        mc = np.empty((k, n), dtype=np.uint32)
+        srk.srk_multi_source(g, sources, C, eps, seed, sc, mc, stats=stats,
+                             no_graph=no_graph, **kw)
+        return sc, mc, stats
+    finally:
+        g.close()
+
+
+def test_batched_sources_bit_exact_against_oracle(srk):
+    # mixed budgets (eps), a zero-in-degree source, a hub and a leaf, in one batch
+    rp, col = rmat_graph(16)
+    deg = np.diff(rp)
+    sources = [int(np.argmax(deg)), int(np.flatnonzero(deg == 0)[3]), 12345,
+               int(np.flatnonzero(deg == 1)[5]), 0]
+    eps = [0.05, 0.1, 0.08, 0.05, 0.2]
+    sc, mc, stats = _multi(srk, rp, col, sources, eps, 23)
+    total = 0
+    for i, s in enumerate(sources):
+        ref = oracle_query(rp, col, s, eps[i], 23)
+        assert np.array_equal(mc[i], ref.count)
+        assert np.array_equal(sc[i], ref.scores)
+        total += int(ref.steps.sum())
+    assert stats.target_steps == total
+
+
+def test_batched_many_batches_graph_and_host_outputs(srk, monkeypatch):
+    # a small scratch budget forces one source per batch; the CUDA-graph path,
+    # the direct path and host outputs must all agree with single queries
+    rp, col = er_graph(1000, 5.0, 1)
+    sources = list(range(0, 40, 3))
+    eps = [0.1 + 0.01 * (i % 5) for i in range(len(sources))]
+    a = _multi(srk, rp, col, sources, eps, 5)
+    monkeypatch.setenv("SRK_BATCH_BYTES", "1")
+    b = _multi(srk, rp, col, sources, eps, 5, no_graph=True)
+    c = _multi(srk, rp, col, sources, eps, 5, device_out=False)
+    for x, y in ((a, b), (a, c)):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        assert x[2].target_steps == y[2].target_steps
+    for i in (0, 7, len(sources) - 1):
+        one = gpu_query(srk, rp, col, sources[i], eps[i], 5)
+        assert np.array_equal(one[0], a[0][i]) and np.array_equal(one[1], a[1][i])
