@@ -60,6 +60,12 @@ def parse():
                     help="approximate CPU time budget of the oracle baseline")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-probe", action="store_true")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch"],
+                    help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
+                         "batched multi-source on R-MAT --batch-scale vs the plain path")
+    ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--batch-sources", type=int, default=12,
+                    help="sources of the 4096-source batching list that are run")
     return ap.parse_args()
 
 
@@ -222,6 +228,70 @@ def cpu_baseline(rp, col, sources, budget_s):
             "steps_per_s": steps / per_query}
 
 
+def run_batch(args, rank, world):
+    """Batched multi-source (srk_multi_source, one persistent launch per
+    batch) against the plain path (one srk_single_source per source) on the
+    same sources and eps: R-MAT scale --batch-scale, 4096 sources of which a
+    third have top in-degree, a third median in-degree and a third none,
+    eps per source from {0.05, 0.02, 0.01}; the first --batch-sources of the
+    list interleaved by group are run."""
+    import torch
+    from srk_inputs import rmat_in_csr_torch, mixed_sources, mixed_eps
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as srk
+    t0 = time.perf_counter()
+    rp_d, col_d = rmat_in_csr_torch(args.batch_scale, seed=GRAPH_SEED, device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    rp = rp_d.cpu().numpy()
+    n, m = rp.size - 1, int(col_d.numel())
+    all_src = mixed_sources(rp, 4096, seed=3)
+    all_eps = mixed_eps(4096, seed=3)
+    third = 4096 // 3
+    order = [g * third + i for i in range(third) for g in range(3)]
+    pick = order[:args.batch_sources]
+    sources = [int(all_src[i]) for i in pick]
+    eps = [float(all_eps[i]) for i in pick]
+    g = srk.srk_graph_load(rp_d, col_d)
+    k = len(sources)
+    out = torch.empty((k, n), dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    # warm-up: the first call autotunes the persistent kernel's launch shape
+    srk.srk_multi_source(g, sources[:3], C, eps[:3], QUERY_SEED, out[:3])
+    torch.cuda.synchronize()
+    st = srk.SrkStats()
+    ev[0].record()
+    srk.srk_multi_source(g, sources, C, eps, QUERY_SEED, out, stats=st)
+    ev[1].record()
+    ev[1].synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / 1e3
+    single = torch.empty(n, dtype=torch.float64, device=dev)
+    t_plain, same = 0.0, True
+    for i, s in enumerate(sources):
+        ev[0].record()
+        srk.srk_single_source(g, s, C, eps[i], QUERY_SEED, single)
+        ev[1].record()
+        ev[1].synchronize()
+        t_plain += ev[0].elapsed_time(ev[1]) / 1e3
+        same = same and bool(torch.equal(single, out[i]))
+    deg = np.diff(rp)
+    line = {"metric": "batched multi-source queries/s (R-MAT scale %d, mixed eps)" % args.batch_scale,
+            "workload": "batch_rmat%d_mixed_sources_mixed_eps" % args.batch_scale,
+            "value": k / t_batch, "unit": "queries/s", "higher_is_better": True,
+            "plain_value": k / t_plain, "batched_over_plain": t_plain / t_batch,
+            "identical_to_plain": same, "sources": k, "n": n, "m": m,
+            "source_in_degrees": [int(deg[s]) for s in sources], "eps": eps,
+            "target_steps": st.target_steps, "walk_steps_per_s": st.target_steps / t_batch,
+            "batch_shape": st.batch_shape, "graph_gen_s": t_gen,
+            "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -263,6 +333,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world) if rank == 0 else 0
 
     import torch
     if not torch.cuda.is_available():

@@ -75,7 +75,8 @@ typedef struct srk_stats {
     int32_t L;              /* truncation length */
     int32_t n_walks;        /* N_tot = sum_l N_l, walks per node and pairs per target */
     int32_t n_active_pairs; /* pairs whose both walks take >= 1 step */
-    int32_t reserved;
+    int32_t batch_shape;    /* srk_multi_source: index of the persistent kernel's
+                               launch shape the autotuner chose; else -1 */
     uint64_t source_steps;  /* steps taken by the source's walks */
     uint64_t target_steps;  /* target-walk steps taken over all targets */
 } srk_stats;

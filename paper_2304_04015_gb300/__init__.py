@@ -55,7 +55,7 @@ class SrkError(RuntimeError):
 class SrkStats(ctypes.Structure):
     _fields_ = [("z", ctypes.c_double), ("L", ctypes.c_int32),
                 ("n_walks", ctypes.c_int32), ("n_active_pairs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("source_steps", ctypes.c_uint64),
+                ("batch_shape", ctypes.c_int32), ("source_steps", ctypes.c_uint64),
                 ("target_steps", ctypes.c_uint64)]
 
 

@@ -596,6 +596,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "srk_multi_source");
   }
+  total.batch_shape = g->batch_cfg;
   if (rc == SRK_OK && opt && opt->stats) *opt->stats = total;
   return rc;
 }

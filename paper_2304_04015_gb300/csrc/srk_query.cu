@@ -439,7 +439,10 @@ int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,
                         cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reading query statistics");
-  if (!accumulate) memset(stats, 0, sizeof *stats);
+  if (!accumulate) {
+    memset(stats, 0, sizeof *stats);
+    stats->batch_shape = -1;
+  }
   stats->z = t.z;
   stats->L = t.L;
   stats->n_walks = t.N_tot;

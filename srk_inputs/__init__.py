@@ -21,7 +21,12 @@ Recipes (the paper has no datasets; these stand in for its graphs):
   probabilities (a, b, c, d) (one float32 uniform per level).  Row = source, column = target of the directed
   edge source -> target, so the source becomes an in-neighbour of the target.
   Self-loops are dropped, duplicates removed, node ids are not permuted.
+* ``rmat_in_csr_torch``: the same R-MAT law drawn with torch's generator on a
+  device (used for scale 22-24, where numpy takes minutes).
 * ``uniform_sources``: distinct nodes drawn uniformly.
+* ``mixed_sources`` / ``mixed_eps``: the batching workload's sources (a third
+  of top in-degree, a third of median in-degree, a third without
+  in-neighbours) and per-source eps drawn from {0.05, 0.02, 0.01}.
 """
 from __future__ import annotations
 
@@ -34,6 +39,8 @@ __all__ = [
     "mixed_sources",
     "lognormal_weights",
     "csr_from_edges",
+    "rmat_in_csr_torch",
+    "mixed_eps",
 ]
 
 
@@ -125,6 +132,53 @@ def rmat_in_csr(scale: int, edge_factor: int = 16,
     if row_ptr[-1] > np.iinfo(np.int32).max:
         raise ValueError("graph has more than 2**31-1 edges")
     return row_ptr.astype(np.int32), col
+
+
+def rmat_in_csr_torch(scale: int, edge_factor: int = 16,
+                      abcd=(0.57, 0.19, 0.19, 0.05), seed: int = 1,
+                      device="cuda", chunk: int = 1 << 26):
+    """The R-MAT recipe of ``rmat_in_csr`` drawn with torch's generator on
+    ``device`` (fast for scale 22-24).  Same law, different random stream, so
+    the graph differs from ``rmat_in_csr`` with the same seed.  Returns int32
+    torch tensors (row_ptr, col) on ``device``."""
+    import torch
+    a, b, c, d = abcd
+    n = 1 << scale
+    n_draws = edge_factor * n
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    t_a, t_ab, t_abc = float(a), float(a + b), float(a + b + c)
+    keys = []
+    done = 0
+    while done < n_draws:
+        e = min(chunk, n_draws - done)
+        src = torch.zeros(e, dtype=torch.int64, device=device)
+        dst = torch.zeros(e, dtype=torch.int64, device=device)
+        for level in range(scale):
+            r = torch.rand(e, generator=gen, device=device, dtype=torch.float32)
+            sh = scale - 1 - level
+            src += (r >= t_ab).to(torch.int64) << sh
+            dst += (((r >= t_a) & (r < t_ab)) | (r >= t_abc)).to(torch.int64) << sh
+        keep = src != dst
+        keys.append(torch.unique(dst[keep] * n + src[keep]))
+        del src, dst, keep
+        done += e
+    key = torch.unique(torch.cat(keys)) if len(keys) > 1 else keys[0]
+    del keys
+    dst_s = key >> scale
+    col = (key & (n - 1)).to(torch.int32)
+    counts = torch.bincount(dst_s, minlength=n)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    if int(row_ptr[-1]) > np.iinfo(np.int32).max:
+        raise ValueError("graph has more than 2**31-1 edges")
+    return row_ptr.to(torch.int32), col
+
+
+def mixed_eps(k: int, seed: int = 3, choices=(0.05, 0.02, 0.01)) -> np.ndarray:
+    """Per-source error targets drawn uniformly from ``choices``."""
+    rng = np.random.default_rng(seed + 1000)
+    return rng.choice(np.asarray(choices, dtype=np.float64), size=k)
 
 
 def uniform_sources(n: int, k: int, seed: int = 2) -> np.ndarray:

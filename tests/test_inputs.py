@@ -45,3 +45,15 @@ def test_sources():
     m = mixed_sources(rp, 12, seed=3)
     deg = np.diff(rp)
     assert m.size == 12 and np.all(deg[m[8:]] == 0)
+
+
+def test_rmat_torch_generator_structure():
+    import torch
+    from srk_inputs import rmat_in_csr_torch, mixed_eps
+    rp, col = rmat_in_csr_torch(11, seed=2, device="cpu")
+    rp, col = rp.numpy(), col.numpy()
+    check_csr(rp, col, 1 << 11)
+    deg = np.diff(rp)
+    assert deg[0] == deg.max() and (deg == 0).mean() > 0.2
+    e = mixed_eps(300, seed=3)
+    assert set(np.unique(e)) == {0.01, 0.02, 0.05}
