@@ -20,6 +20,9 @@ Contents (each function cites the passage of the paper it restates):
   published definition (Salmon et al., SC'11).
 * ``alg2``    -- a literal restatement of Algorithm 2 (tuples, lexicographic
   sort, labels, PREDECESSOR, deduplicated walk-meet messages) for tiny graphs.
+* ``linear``  -- the truncated linearised single-source form of Appendix A
+  (s = sum_t c^t (P^T)^t D P^t e_s, D = (1-c)I) in FP64, its reverse-mode
+  gradient w.r.t. edge weights (torch CPU autograd) and finite differences.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 against closed forms, invariants, brute force or published test vectors; no
