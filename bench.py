@@ -60,7 +60,7 @@ def parse():
                     help="approximate CPU time budget of the oracle baseline")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-probe", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "linear"],
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
@@ -292,6 +292,66 @@ def run_batch(args, rank, world):
     return 0
 
 
+def run_linear(args, rank, world):
+    """Linearised single-source SimRank, forward + adjoint backward: R-MAT
+    scale 18, edge factor 16, lognormal(0, 0.5) FP32 weights, L = 10, c = 0.6,
+    D = (1-c)I, loss = sum_v w_v s(s, v) with w ~ N(0, 1); one step = one
+    forward and one backward for the next source of a uniform list."""
+    import torch
+    from srk_inputs import rmat_in_csr, lognormal_weights, uniform_sources
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as srk
+    rp, col = rmat_in_csr(18, seed=GRAPH_SEED)
+    n, m = rp.size - 1, col.size
+    w = torch.from_numpy(lognormal_weights(m, seed=4)).to(dev)
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    deg = np.diff(rp)
+    srcs = [int(x) for x in uniform_sources(n, 64, seed=SOURCE_SEED) if deg[x] > 0]
+    lw = torch.from_numpy(np.random.default_rng(5).normal(size=n).astype(np.float32)).to(dev)
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    gw = torch.empty(m, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    L = 10
+
+    def step(i):
+        ctx = srk.srk_linear_fwd(g, w, srcs[i % len(srcs)], C, L, out)
+        ev[1].record()
+        srk.srk_linear_bwd(ctx, lw, gw)
+        return ctx
+
+    for i in range(args.warmup):
+        step(i).free()
+    fwd_ms, bwd_ms = [], []
+    for i in range(args.steps):
+        ev[0].record()
+        ctx = step(i)
+        ev[2].record()
+        ev[2].synchronize()
+        fwd_ms.append(ev[0].elapsed_time(ev[1]))
+        bwd_ms.append(ev[1].elapsed_time(ev[2]))
+        ctx.free()
+    t = (np.sum(fwd_ms) + np.sum(bwd_ms)) / 1e3
+    # bytes streamed: forward 2L sparse passes (P^t e_s, partial sums) over the
+    # in-CSR (col 4 B + P 4 B + row 4 B per edge); backward 2L passes plus the
+    # edge-gradient pass (2L vector reads per edge)
+    per_pass = 12.0 * m
+    fwd_bytes = 2 * L * per_pass
+    bwd_bytes = 2 * L * per_pass + m * (8 + 4 * 2 * L)
+    line = {"metric": "linearised SimRank forward+backward per second (R-MAT 18, L=10)",
+            "workload": "linear_rmat18_L10_lognormal_weights", "value": args.steps / t,
+            "unit": "fwd+bwd/s", "higher_is_better": True, "n": n, "m": m,
+            "fwd_ms": float(np.mean(fwd_ms)), "bwd_ms": float(np.mean(bwd_ms)),
+            "fwd_GBps_streamed": fwd_bytes / (np.mean(fwd_ms) / 1e3) / 1e9,
+            "bwd_GBps_streamed": bwd_bytes / (np.mean(bwd_ms) / 1e3) / 1e9,
+            "dtype": "f32", "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -335,6 +395,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch(args, rank, world) if rank == 0 else 0
+    if args.workload == "linear":
+        return run_linear(args, rank, world) if rank == 0 else 0
 
     import torch
     if not torch.cuda.is_available():

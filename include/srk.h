@@ -180,6 +180,47 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
                      uint32_t *meet_counts, void *cuda_stream);
 
 /*
+ * srk_linear_fwd -- truncated linearised single-source SimRank (Appendix A:
+ * S = c P^T S P + D, truncated to L + 1 terms, as in the DISK discussion):
+ *     s_out = sum_{t=0}^{L} c^t (P^T)^t D P^t e_s,   D = (1 - c) I,
+ * with P the column-normalised in-edge weight matrix,
+ * P[u][a] = w(u -> a) / sum_{u' in I(a)} w(u' -> a).  D = (1 - c) I is a
+ * simplification: the paper's D is a correction matrix that is estimated.
+ *   g      : the graph; its in-lists give the edges (edge e = entry e of col).
+ *   edge_w : m positive finite FP32 weights aligned with col (device memory),
+ *            or NULL for the weights given to srk_graph_load.
+ *   s, c   : source (0 <= s < n) and decay (0 < c < 1).
+ *   L      : last term, 0 <= L <= SRK_MAX_LEN.
+ *   s_out  : n FP32 outputs (device memory).
+ *   ctx    : NULL, or receives the context the backward needs (device
+ *            memory for P, the vectors P^t e_s and the partial sums, about
+ *            (2L + 4) n + 2m words); release it with srk_linear_ctx_free.
+ *            The context refers to g, which must outlive it.
+ *   cuda_stream : stream to run on; the call synchronises it (to report
+ *            non-positive weights as SRK_EINVAL).
+ * Arithmetic is FP32; P v is accumulated in FP64 atomics (order-independent
+ * up to FP64 rounding) and P^T v by fixed-order warp reductions.
+ */
+int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s, double c,
+                   int32_t L, float *s_out, srk_linear_ctx **ctx, void *cuda_stream);
+
+/*
+ * srk_linear_bwd -- gradient of a loss w.r.t. the edge weights, by the adjoint
+ * of the forward recursions.
+ *   ctx    : from srk_linear_fwd (not freed here; one backward at a time).
+ *   grad_s : n FP32, dLoss/ds_out (device memory).
+ *   grad_w : m FP32 outputs, dLoss/dw_e (device memory).  Because P is
+ *            invariant to scaling a node's in-weights, sum_{e in I(a)} w_e
+ *            grad_w[e] = 0 for every node a (up to rounding).
+ * Enqueues work on cuda_stream without synchronising.
+ */
+int srk_linear_bwd(srk_linear_ctx *ctx, const float *grad_s, float *grad_w,
+                   void *cuda_stream);
+
+/* srk_linear_ctx_free -- release a context (waits for the device); NULL ok. */
+int srk_linear_ctx_free(srk_linear_ctx *ctx);
+
+/*
  * srk_single_source_noalloc -- srk_single_source that allocates nothing.
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory while they issue queries (an application whose

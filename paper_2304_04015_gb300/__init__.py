@@ -23,7 +23,8 @@ __all__ = [
     "SrkError", "SrkOpts", "SrkStats", "Graph",
     "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
     "srk_multi_source", "srk_single_source_noalloc", "srk_probe_gather",
-    "srk_last_error",
+    "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free", "LinearContext",
+    "LinearSimRank", "linear_simrank", "srk_last_error",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
     "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_OPT_NO_GRAPH", "SRK_MAX_LEN",
@@ -81,10 +82,14 @@ _lib.srk_multi_source.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double,
                                   _vp, _vp, _vp]
 _lib.srk_probe_gather.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
                                   _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+_lib.srk_linear_fwd.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                _vp, ctypes.POINTER(_vp), _vp]
+_lib.srk_linear_bwd.argtypes = [_vp, _vp, _vp, _vp]
+_lib.srk_linear_ctx_free.argtypes = [_vp]
 _lib.srk_last_error.restype = ctypes.c_char_p
 for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
            "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
-           "srk_probe_gather"):
+           "srk_probe_gather", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -293,3 +298,87 @@ def srk_probe_gather(data, iters: int, seed: int, sink, stream=None) -> int:
     del k1, k2
     _check(rc)
     return loads.value
+
+
+class LinearContext:
+    """Owns an ``srk_linear_ctx*`` (the state srk_linear_bwd needs)."""
+
+    def __init__(self, handle: int, graph: "Graph", m: int):
+        self.handle = handle
+        self.graph = graph   # the context refers to the graph
+        self.m = m
+
+    def free(self) -> None:
+        if self.handle:
+            h, self.handle = self.handle, 0
+            _check(_lib.srk_linear_ctx_free(h))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def srk_linear_fwd(g: Graph, edge_w, s: int, c: float, L: int, s_out, *,
+                   keep_context: bool = True, stream=None):
+    """Truncated linearised single-source SimRank into ``s_out`` (device
+    float32, n).  ``edge_w``: device float32 weights aligned with col, or None
+    for the weights given at load.  Returns a LinearContext (or None)."""
+    wp, _, k1 = _ptr(edge_w, "float32")
+    op, _, k2 = _ptr(s_out, "float32")
+    h = _vp()
+    rc = _lib.srk_linear_fwd(g.handle, wp, int(s), float(c), int(L), op,
+                             ctypes.byref(h) if keep_context else None,
+                             _stream_handle(stream))
+    del k1, k2
+    _check(rc)
+    return LinearContext(h.value, g, g.m) if keep_context else None
+
+
+def srk_linear_bwd(ctx: LinearContext, grad_s, grad_w, stream=None) -> None:
+    """dLoss/dw into ``grad_w`` (device float32, m) from ``grad_s`` (n)."""
+    gp, _, k1 = _ptr(grad_s, "float32")
+    wp, _, k2 = _ptr(grad_w, "float32")
+    rc = _lib.srk_linear_bwd(ctx.handle, gp, wp, _stream_handle(stream))
+    del k1, k2
+    _check(rc)
+
+
+def srk_linear_ctx_free(ctx: LinearContext) -> None:
+    ctx.free()
+
+
+def _make_linear_function():
+    import torch
+
+    class LinearSimRank(torch.autograd.Function):
+        """s_vec = sum_t c^t (P^T)^t D P^t e_s as a differentiable function of
+        the edge weights (forward: srk_linear_fwd; backward: srk_linear_bwd)."""
+
+        @staticmethod
+        def forward(ctx, edge_w, graph, s, c, L):
+            out = torch.empty(graph.n, dtype=torch.float32, device=edge_w.device)
+            ctx.lin = srk_linear_fwd(graph, edge_w.detach().contiguous(), s, c, L, out)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            grad_w = torch.empty(ctx.lin.m, dtype=torch.float32, device=grad_out.device)
+            srk_linear_bwd(ctx.lin, grad_out.contiguous().to(torch.float32), grad_w)
+            torch.cuda.current_stream(grad_out.device).synchronize()
+            ctx.lin.free()
+            return grad_w, None, None, None, None
+
+    return LinearSimRank
+
+
+try:
+    LinearSimRank = _make_linear_function()
+except ImportError:  # pragma: no cover
+    LinearSimRank = None
+
+
+def linear_simrank(graph: Graph, edge_w, s: int, c: float = 0.6, L: int = 10):
+    """Differentiable linearised single-source SimRank (torch tensors)."""
+    return LinearSimRank.apply(edge_w, graph, s, c, L)

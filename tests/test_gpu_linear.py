@@ -1,0 +1,124 @@
+"""GPU parity of the linearised form (srk_linear_fwd / srk_linear_bwd).
+
+Forward against the FP64 oracle, backward against the oracle's reverse-mode
+gradient on every edge and against FP64 central finite differences on 256
+sampled edges (edge-weighted R-MAT scale 18, lognormal(0, 0.5) weights, L=10,
+c=0.6, D=(1-c)I, loss = sum_v w_v s(s, v), w ~ N(0, 1)).
+
+Tolerances (FP32 arithmetic, FP64 references): forward
+|d| <= 1e-5 |ref| + 1e-7 max|ref|; gradient |d| <= 1e-4 |ref| + 1e-4 rms(ref)
+per edge.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+C = 0.6
+
+
+@pytest.fixture(scope="module")
+def srk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as m
+    return m
+
+
+@functools.lru_cache(maxsize=None)
+def weighted(kind, size, seed):
+    from srk_inputs import er_in_csr, rmat_in_csr, lognormal_weights
+    rp, col = er_in_csr(size, 4.0, seed=seed) if kind == "er" else rmat_in_csr(size, seed=seed)
+    return rp, col, lognormal_weights(col.size, seed=seed + 10)
+
+
+def run_gpu(srk, rp, col, w, s, L, g):
+    import torch
+    dev = torch.device("cuda:0")
+    n = rp.size - 1
+    graph = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        wt = torch.from_numpy(w).to(dev).requires_grad_(True)
+        out = srk.linear_simrank(graph, wt, s, C, L)
+        loss = (torch.from_numpy(g.astype(np.float32)).to(dev) * out).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        return out.detach().cpu().numpy().astype(np.float64), wt.grad.cpu().numpy().astype(np.float64)
+    finally:
+        graph.close()
+
+
+def check_forward(got, ref):
+    tol = 1e-5 * np.abs(ref) + 1e-7 * np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= tol)
+
+
+def check_grad(got, ref):
+    rms = np.sqrt(np.mean(ref ** 2))
+    tol = 1e-4 * np.abs(ref) + 1e-4 * rms
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+
+
+def test_small_graph_against_reverse_mode_oracle(srk):
+    from oracle import linear
+    rp, col, w = weighted("er", 500, 3)
+    g = np.random.default_rng(4).normal(size=500)
+    for s, L in ((0, 10), (17, 3), (5, 1)):
+        out, gr = run_gpu(srk, rp, col, w, s, L, g)
+        ref_g, ref_s = linear.grad(rp, col, w.astype(np.float64), 500, s, C, L, g)
+        check_forward(out, ref_s)
+        check_grad(gr, ref_g)
+
+
+def test_rmat18_configuration_gradients(srk):
+    from oracle import linear
+    rp, col, w = weighted("rmat", 18, 1)
+    n = rp.size - 1
+    deg = np.diff(rp)
+    s = int(np.argsort(-deg)[10])
+    g = np.random.default_rng(6).normal(size=n)
+    out, gr = run_gpu(srk, rp, col, w, s, 10, g)
+    w64 = w.astype(np.float64)
+    ref_g, ref_s = linear.grad(rp, col, w64, n, s, C, 10, g)
+    check_forward(out, ref_s)
+    check_grad(gr, ref_g)
+    # FP64 central finite differences on 256 sampled edges
+    rng = np.random.default_rng(7)
+    edges = rng.choice(col.size, 256, replace=False)
+    fd = linear.finite_difference_pool(rp, col, w64, n, s, C, 10, g, edges)
+    check_grad(gr[edges], fd)
+    # scaling invariance of each in-list (P is unchanged): exact for the
+    # oracle, and for the FP32 gradient within the per-edge tolerance above
+    a_of_e = np.repeat(np.arange(n), deg)
+    row_dot = np.bincount(a_of_e, weights=w64 * gr, minlength=n)
+    rms = np.sqrt(np.mean(ref_g ** 2))
+    row_tol = np.bincount(a_of_e, weights=w64 * (1e-4 * np.abs(ref_g) + 1e-4 * rms), minlength=n)
+    assert np.all(np.abs(row_dot) <= row_tol + 1e-30)
+
+
+def test_linear_invalid_weights_and_source(srk):
+    import torch
+    rp, col, w = weighted("er", 100, 2)
+    dev = torch.device("cuda:0")
+    graph = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        out = torch.empty(100, dtype=torch.float32, device=dev)
+        bad = torch.from_numpy(w).to(dev)
+        bad[3] = -1.0
+        with pytest.raises(srk.SrkError) as e:
+            srk.srk_linear_fwd(graph, bad, 0, C, 10, out)
+        assert e.value.code == srk.SRK_EINVAL
+        with pytest.raises(srk.SrkError):
+            srk.srk_linear_fwd(graph, torch.from_numpy(w).to(dev), 100, C, 10, out)
+        with pytest.raises(srk.SrkError):   # no weights given and none loaded
+            srk.srk_linear_fwd(graph, None, 0, C, 10, out)
+        ctx = srk.srk_linear_fwd(graph, torch.from_numpy(w).to(dev), 0, C, 0, out)
+        gw = torch.empty(col.size, dtype=torch.float32, device=dev)
+        srk.srk_linear_bwd(ctx, torch.ones(100, device=dev), gw)
+        torch.cuda.synchronize()
+        assert float(gw.abs().max()) == 0.0 and float(out[0]) == pytest.approx(1 - C)
+        ctx.free()
+    finally:
+        graph.close()

@@ -30,6 +30,23 @@ def test_sparse_forward_equals_dense_powers():
         assert np.abs(a - b).max() < 1e-14
 
 
+def test_horner_form_equals_the_literal_sum():
+    rp, col, w = small_graph(60, seed=11)
+    for L in (0, 1, 4, 10):
+        a = linear.forward(rp, col, w, 60, 3, C, L)
+        b = linear.forward_horner(rp, col, w, 60, 3, C, L)
+        assert np.abs(a - b).max() < 1e-15
+
+
+def test_finite_difference_pool_matches_serial():
+    rp, col, w = small_graph(30, seed=5)
+    g = np.random.default_rng(1).normal(size=30)
+    edges = [0, 3, 7]
+    a = linear.finite_difference(rp, col, w, 30, 2, C, 5, g, edges)
+    b = linear.finite_difference_pool(rp, col, w, 30, 2, C, 5, g, edges, processes=2)
+    assert np.abs(a - b).max() < 1e-9
+
+
 def test_one_edge_closed_form():
     # I(a) = {u}, a = 1, u = 0: s_vec = (1-c) e_a + c (1-c) P^T e_u = (1 - c^2) e_a
     rp = np.array([0, 0, 1], dtype=np.int32)
