@@ -60,10 +60,16 @@ def parse():
                     help="approximate CPU time budget of the oracle baseline")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-probe", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "linear"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "linear", "serve"],
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-budget-mb", type=int, default=1024)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-target-ms", type=float, default=1000.0,
+                    help="serve: latency target of the admission (0: memory only, FIFO)")
     ap.add_argument("--batch-sources", type=int, default=12,
                     help="sources of the 4096-source batching list that are run")
     return ap.parse_args()
@@ -352,6 +358,86 @@ def run_linear(args, rank, world):
     return 0
 
 
+def run_serve(args, rank, world):
+    """Serving: three resident R-MAT graphs (scales 16, 20, 23, edge factor
+    16); single-source requests arrive Poisson at --rate per second for
+    --serve-seconds; each picks a graph uniformly, eps uniformly from
+    {0.05, 0.02, 0.01} and a source uniformly; the server admits a request
+    when its device memory fits in --serve-budget-mb and sheds it otherwise.
+    Reports admitted queries/s and p50/p99 latency (submission to scores on
+    the host), beside the same admitted requests run one at a time."""
+    import torch
+    from srk_inputs import rmat_in_csr, rmat_in_csr_torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as srk
+    graphs, sizes = [], []
+    for scale in (16, 20, 23):
+        if scale <= 20:
+            rp, col = rmat_in_csr(scale, seed=GRAPH_SEED)
+            rp_d, col_d = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+        else:
+            rp_d, col_d = rmat_in_csr_torch(scale, seed=GRAPH_SEED, device=dev)
+        graphs.append(srk.srk_graph_load(rp_d, col_d))
+        sizes.append(int(rp_d.numel()) - 1)
+    rng = np.random.default_rng(4)
+    horizon = args.serve_seconds
+    t_arr = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * horizon * 1.2) + 16))
+    t_arr = t_arr[t_arr < horizon]
+    reqs = []
+    for _ in range(t_arr.size):
+        gi = int(rng.integers(0, 3))
+        reqs.append((gi, int(rng.integers(0, sizes[gi])), float(rng.choice([0.05, 0.02, 0.01]))))
+    budget = int(args.serve_budget_mb) << 20
+    # warm-up (module load, pools, first launches) outside the measured run
+    for gi in range(3):
+        out = torch.empty(sizes[gi], dtype=torch.float64, device=dev)
+        srk.srk_single_source(graphs[gi], 0, C, 0.05, 1, out)
+    torch.cuda.synchronize()
+    admitted = []
+    with srk.srk_server_create(graphs, budget, args.serve_workers,
+                               args.serve_target_ms) as srv:
+        t0 = time.perf_counter()
+        for k, (gi, s, eps) in enumerate(reqs):
+            while time.perf_counter() - t0 < t_arr[k]:
+                pass
+            if srk.srk_server_submit(srv, gi, s, C, eps, QUERY_SEED + k):
+                admitted.append(k)
+        t_submit_end = time.perf_counter() - t0
+        srk.srk_server_drain(srv)
+        st = srk.srk_server_stats(srv)
+    # the admitted requests again, one at a time (the plain path)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    outs = [torch.empty(n, dtype=torch.float64, device=dev) for n in sizes]
+    t_plain = 0.0
+    for k in admitted:
+        gi, s, eps = reqs[k]
+        ev[0].record()
+        srk.srk_single_source(graphs[gi], s, C, eps, QUERY_SEED + k, outs[gi])
+        ev[1].record()
+        ev[1].synchronize()
+        t_plain += ev[0].elapsed_time(ev[1]) / 1e3
+    line = {"metric": "served single-source SimRank queries/s and latency (R-MAT 16/20/23)",
+            "workload": "serve_rmat16_20_23_poisson", "value": st.queries_per_s,
+            "unit": "queries/s", "higher_is_better": True,
+            "offered_per_s": args.rate, "seconds": horizon, "submitted": st.submitted,
+            "admitted": st.admitted, "shed": st.shed, "shed_fraction": st.shed / max(1, st.submitted),
+            "completed": st.completed, "failed": st.failed,
+            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms, "max_ms": st.max_ms,
+            "wall_s": st.wall_s, "target_steps": st.target_steps,
+            "reserved_peak_MB": st.reserved_peak / 2 ** 20, "budget_MB": args.serve_budget_mb,
+            "workers": args.serve_workers, "latency_target_ms": args.serve_target_ms,
+            "submit_loop_s": t_submit_end,
+            "plain_one_at_a_time_queries_per_s": len(admitted) / t_plain if t_plain else None,
+            "graph_nodes": sizes}
+    print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.close()
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -397,6 +483,8 @@ def main():
         return run_batch(args, rank, world) if rank == 0 else 0
     if args.workload == "linear":
         return run_linear(args, rank, world) if rank == 0 else 0
+    if args.workload == "serve":
+        return run_serve(args, rank, world) if rank == 0 else 0
 
     import torch
     if not torch.cuda.is_available():

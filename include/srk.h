@@ -57,6 +57,10 @@ extern "C" {
 /* srk_opts.flags */
 #define SRK_OPT_NO_GRAPH 1  /* srk_multi_source: enqueue launches directly
                                instead of through a captured CUDA graph */
+#define SRK_OPT_WARMUP_RULE 2  /* sample counts of the warm-up algorithm
+                                  (Section 3): z = ln(2 n^2) / (2 eps^2),
+                                  L = floor(3 ln(n / eps) / ln(1/sqrt c));
+                                  p and q are then not used */
 
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */
@@ -87,7 +91,7 @@ typedef struct srk_opts {
                               eps is then not used */
     int32_t  L_override;   /* >= 0: truncation length instead of
                               floor(p ln n / ln(1/sqrt(c))); < 0: paper */
-    int32_t  flags;        /* 0, or SRK_OPT_NO_GRAPH (srk_multi_source only) */
+    int32_t  flags;        /* SRK_OPT_* bits (SRK_OPT_NO_GRAPH: multi-source only) */
     double   p;            /* threshold knob of Appendix B.5, >= 1 (0 means 1) */
     double   q;            /* failure knob of Appendix B.5, >= 1 (0 means 1) */
     uint32_t *step_counts; /* NULL or n entries (host or device memory):
@@ -96,6 +100,11 @@ typedef struct srk_opts {
     void     *timing_events; /* NULL or a host array of two cudaEvent_t: [0] is
                               recorded on the query's stream just before the
                               target-walk kernel (step a4), [1] just after */
+    int32_t  target_begin; /* with target_end: compute and write only the
+                              targets u in [target_begin, target_end); 0, 0 =
+                              all.  The paper's owner rule (Section 5.5): a
+                              query split by node range across devices */
+    int32_t  target_end;
 } srk_opts;
 
 /*
@@ -258,6 +267,52 @@ int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c,
  */
 int srk_probe_gather(const int32_t *data, int64_t n, int64_t iters, uint32_t seed,
                      unsigned long long *sink, int64_t *loads, void *cuda_stream);
+
+/*
+ * Query server (no counterpart in the paper; the serving configuration):
+ * resident graphs, memory-based admission, worker threads with one CUDA
+ * stream each, latency statistics.
+ *
+ * srk_server_create -- graphs: n_graphs loaded handles (they must outlive the
+ *   server); mem_budget: device bytes that admitted, unfinished requests may
+ *   hold (each request holds its query scratch plus its n-entry score vector);
+ *   n_workers: worker threads / streams (1..64); latency_target_ms: 0 for
+ *   memory-only admission and first-in-first-out service, else a target for
+ *   the estimated time to finish all admitted work including the new request,
+ *   with shortest-estimated-work-first service.  The estimate is (nodes with
+ *   in-neighbours) x N_tot x 0.8 walk steps per request (0 when the source
+ *   has no in-neighbours), divided by the rate at which completed requests
+ *   got through their estimate (exponential average, starting at 5e10/s).  Copies each graph's row_ptr to the host once.
+ * srk_server_submit -- enqueue one srk_single_source query on graph index
+ *   `graph`.  The request is admitted if the memory it needs fits in what the
+ *   budget leaves (and, with a latency target, its estimated finish fits the
+ *   target); otherwise it is shed (*admitted = 0; not an error).
+ *   host_scores: NULL, or n host doubles that receive the scores before the
+ *   request counts as completed (caller keeps them alive until then).  tag is
+ *   reserved for the caller.  Invalid arguments return SRK_EINVAL.
+ * srk_server_drain -- wait until every admitted request has completed.
+ * srk_server_stats -- counters and the latency (submission to scores on the
+ *   host) percentiles of completed requests.
+ * srk_server_destroy -- finish queued requests, stop the workers, free.
+ */
+typedef struct srk_server srk_server;
+typedef struct srk_server_report {
+    uint64_t submitted, admitted, shed, completed, failed;
+    uint64_t target_steps;   /* walk steps of completed requests */
+    uint64_t reserved_peak;  /* most device memory held by admitted requests */
+    double p50_ms, p99_ms, mean_ms, max_ms;
+    double wall_s;           /* first submission to last completion */
+    double queries_per_s;    /* completed / wall_s */
+} srk_server_report;
+
+int srk_server_create(const srk_graph *const *graphs, int32_t n_graphs,
+                      uint64_t mem_budget, int32_t n_workers, double latency_target_ms,
+                      srk_server **out);
+int srk_server_submit(srk_server *srv, int32_t graph, int32_t s, double c, double eps,
+                      uint64_t seed, double *host_scores, uint64_t tag, int32_t *admitted);
+int srk_server_drain(srk_server *srv);
+int srk_server_stats(srk_server *srv, srk_server_report *report);
+int srk_server_destroy(srk_server *srv);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *srk_last_error(void);

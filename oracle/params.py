@@ -58,13 +58,15 @@ class Table:
 
 def sample_table(n: int, c: float, eps: float, *, p: float = 1.0,
                  q: float = 1.0, z_override: Optional[float] = None,
-                 L_override: Optional[int] = None) -> Table:
+                 L_override: Optional[int] = None, warmup_rule: bool = False) -> Table:
     """Build the per-length walk counts for a query on a graph of n nodes.
 
     Follows Algorithm 1 lines 3-5, Algorithm 2 line 2 and Appendix B.5.
     ``z_override`` / ``L_override`` replace the paper's formulas for z and the
     truncation length (used by the small configuration that fixes both).
-    When z is overridden, eps is not used.
+    When z is overridden, eps is not used.  ``warmup_rule`` takes the sample
+    size and truncation of the warm-up algorithm of Section 3 instead:
+    z = ln(2 n^2) / (2 eps^2) and L = floor(3 log_{1/sqrt c}(n / eps)).
     """
     if n < 1:
         raise ValueError("n must be >= 1")
@@ -75,6 +77,10 @@ def sample_table(n: int, c: float, eps: float, *, p: float = 1.0,
     rc = math.sqrt(c)
     if z_override is not None and z_override > 0:
         z = float(z_override)
+    elif warmup_rule:
+        if not (0.0 < eps < 1.0):
+            raise ValueError("eps must lie in (0, 1)")
+        z = math.log(2.0 * n * n) / (2.0 * eps * eps)
     else:
         thr = 3.0 / math.pow(n, p)
         if not (thr < eps < 1.0):
@@ -83,6 +89,10 @@ def sample_table(n: int, c: float, eps: float, *, p: float = 1.0,
         z = math.log(2.0 * math.pow(n, q)) / (2.0 * lam * lam)
     if L_override is not None and L_override >= 0:
         L = int(L_override)
+    elif warmup_rule:
+        if not (0.0 < eps < 1.0):
+            raise ValueError("eps must lie in (0, 1)")
+        L = int(math.floor(3.0 * math.log(float(n) / eps) / (-math.log(rc))))
     else:
         L = int(math.floor(p * math.log(float(n)) / (-math.log(rc))))
     N, P, a, Z = [], [0], [], []

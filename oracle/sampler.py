@@ -135,10 +135,10 @@ class Result:
 
 def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
         targets=None, z_override=None, L_override=None, p: float = 1.0,
-        q: float = 1.0, threads: int = 0) -> Result:
+        q: float = 1.0, warmup_rule: bool = False, threads: int = 0) -> Result:
     """One single-source query, steps a1-a5, for ``targets`` (all nodes if None)."""
     tab = sample_table(n, c, eps, p=p, q=q, z_override=z_override,
-                       L_override=L_override)
+                       L_override=L_override, warmup_rule=warmup_rule)
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
     cl = np.ascontiguousarray(col, dtype=np.int32)
     if targets is None:

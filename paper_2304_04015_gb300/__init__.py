@@ -24,16 +24,18 @@ __all__ = [
     "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
     "srk_multi_source", "srk_single_source_noalloc", "srk_probe_gather",
     "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free", "LinearContext",
-    "LinearSimRank", "linear_simrank", "srk_last_error",
+    "LinearSimRank", "linear_simrank", "SrkServerReport", "Server",
+    "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
+    "srk_server_destroy", "srk_last_error",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
-    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_OPT_NO_GRAPH", "SRK_MAX_LEN",
+    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_OPT_NO_GRAPH", "SRK_OPT_WARMUP_RULE", "SRK_MAX_LEN",
     "SRK_MAX_WALKS",
 ]
 
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
 SRK_DEVICE_PTRS, SRK_VALIDATE = 1, 2
-SRK_OPT_NO_GRAPH = 1
+SRK_OPT_NO_GRAPH, SRK_OPT_WARMUP_RULE = 1, 2
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
 SRK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -64,7 +66,8 @@ class SrkOpts(ctypes.Structure):
     _fields_ = [("z_override", ctypes.c_double), ("L_override", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("p", ctypes.c_double),
                 ("q", ctypes.c_double), ("step_counts", ctypes.c_void_p),
-                ("stats", ctypes.POINTER(SrkStats)), ("timing_events", ctypes.c_void_p)]
+                ("stats", ctypes.POINTER(SrkStats)), ("timing_events", ctypes.c_void_p),
+                ("target_begin", ctypes.c_int32), ("target_end", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -86,10 +89,32 @@ _lib.srk_linear_fwd.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double, ctype
                                 _vp, ctypes.POINTER(_vp), _vp]
 _lib.srk_linear_bwd.argtypes = [_vp, _vp, _vp, _vp]
 _lib.srk_linear_ctx_free.argtypes = [_vp]
+
+
+class SrkServerReport(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("shed", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("target_steps", ctypes.c_uint64),
+                ("reserved_peak", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("queries_per_s", ctypes.c_double)]
+
+
+_lib.srk_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.c_int32, ctypes.c_double, ctypes.POINTER(_vp)]
+_lib.srk_server_submit.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_uint64, _vp, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_int32)]
+_lib.srk_server_drain.argtypes = [_vp]
+_lib.srk_server_stats.argtypes = [_vp, ctypes.POINTER(SrkServerReport)]
+_lib.srk_server_destroy.argtypes = [_vp]
 _lib.srk_last_error.restype = ctypes.c_char_p
 for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
            "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
-           "srk_probe_gather", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free"):
+           "srk_probe_gather", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free",
+           "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
+           "srk_server_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -203,8 +228,13 @@ def srk_graph_info(g: Graph):
 
 
 def _opts(z_override=None, L_override=None, p=None, q=None, step_counts=None,
-          stats: Optional[SrkStats] = None, timing_events=None, flags: int = 0):
+          stats: Optional[SrkStats] = None, timing_events=None, flags: int = 0,
+          target_range=None, warmup_rule: bool = False):
     o = SrkOpts()
+    if target_range is not None:
+        o.target_begin, o.target_end = int(target_range[0]), int(target_range[1])
+    if warmup_rule:
+        flags |= SRK_OPT_WARMUP_RULE
     o.z_override = float(z_override) if z_override else 0.0
     o.L_override = int(L_override) if L_override is not None else -1
     o.flags = int(flags)
@@ -226,7 +256,8 @@ def srk_single_source(g: Graph, s: int, c: float, eps: float, seed: int,
                       scores, meet_counts=None, weight_sums=None, *,
                       z_override=None, L_override=None, p=None, q=None,
                       step_counts=None, stats: Optional[SrkStats] = None,
-                      timing_events=None, stream=None) -> None:
+                      timing_events=None, target_range=None, warmup_rule: bool = False,
+                      stream=None) -> None:
     """One query (``srk_single_source``): fills ``scores`` (n float64) and,
     when given, ``meet_counts`` (n uint32), ``weight_sums`` (n uint64),
     ``step_counts`` (n uint32) and ``stats``.  ``timing_events``: two
@@ -235,7 +266,8 @@ def srk_single_source(g: Graph, s: int, c: float, eps: float, seed: int,
     sc, _, k1 = _ptr(scores, "float64")
     mc, _, k2 = _ptr(meet_counts, "uint32")
     ws, _, k3 = _ptr(weight_sums, "uint64")
-    o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events)
+    o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events,
+                  target_range=target_range, warmup_rule=warmup_rule)
     rc = _lib.srk_single_source(g.handle, int(s), float(c), float(eps),
                                 int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                                 sc, mc, ws, _stream_handle(stream))
@@ -247,7 +279,8 @@ def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
                               scores, meet_counts=None, weight_sums=None, *,
                               z_override=None, L_override=None, p=None, q=None,
                               step_counts=None, stats: Optional[SrkStats] = None,
-                              timing_events=None, stream=None) -> None:
+                              timing_events=None, target_range=None,
+                              warmup_rule: bool = False, stream=None) -> None:
     """``srk_single_source`` for callers that must not allocate device memory
     while querying: the scratch is a static device array of
     ``SRK_NOALLOC_SCRATCH_BYTES``; outputs must be device tensors; calls that
@@ -255,7 +288,8 @@ def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
     sc, _, k1 = _ptr(scores, "float64")
     mc, _, k2 = _ptr(meet_counts, "uint32")
     ws, _, k3 = _ptr(weight_sums, "uint64")
-    o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events)
+    o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events,
+                  target_range=target_range, warmup_rule=warmup_rule)
     rc = _lib.srk_single_source_noalloc(g.handle, int(s), float(c), float(eps),
                                         int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                                         sc, mc, ws, _stream_handle(stream))
@@ -266,7 +300,8 @@ def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
 def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
                      meet_counts=None, *, z_override=None, L_override=None,
                      p=None, q=None, stats: Optional[SrkStats] = None,
-                     no_graph: bool = False, stream=None) -> None:
+                     no_graph: bool = False, warmup_rule: bool = False,
+                     stream=None) -> None:
     """k queries (``srk_multi_source``): ``sources`` and ``eps`` are host
     sequences of length k; ``scores`` is k x n float64.  ``no_graph``: enqueue
     the batch launches directly instead of through a captured CUDA graph."""
@@ -276,7 +311,7 @@ def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
     sc, _, k1 = _ptr(scores, "float64")
     mc, _, k2 = _ptr(meet_counts, "uint32")
     o, _ = _opts(z_override, L_override, p, q, None, stats,
-                 flags=SRK_OPT_NO_GRAPH if no_graph else 0)
+                 flags=SRK_OPT_NO_GRAPH if no_graph else 0, warmup_rule=warmup_rule)
     rc = _lib.srk_multi_source(g.handle, src.ctypes.data, k, float(c), eps_a.ctypes.data,
                                int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), sc, mc,
                                _stream_handle(stream))
@@ -382,3 +417,72 @@ except ImportError:  # pragma: no cover
 def linear_simrank(graph: Graph, edge_w, s: int, c: float = 0.6, L: int = 10):
     """Differentiable linearised single-source SimRank (torch tensors)."""
     return LinearSimRank.apply(edge_w, graph, s, c, L)
+
+
+class Server:
+    """A query server (``srk_server*``) over resident graphs."""
+
+    def __init__(self, handle: int, graphs):
+        self.handle = handle
+        self.graphs = list(graphs)   # the server refers to them
+        self._buffers = []
+
+    def close(self) -> None:
+        if self.handle:
+            h, self.handle = self.handle, 0
+            _check(_lib.srk_server_destroy(h))
+            self._buffers = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def srk_server_create(graphs, mem_budget: int, n_workers: int = 4,
+                      latency_target_ms: float = 0.0) -> Server:
+    """A server over ``graphs``; ``latency_target_ms`` > 0 adds estimated-
+    finish-time admission and shortest-estimated-work-first service."""
+    arr = (_vp * len(graphs))(*[g.handle for g in graphs])
+    h = _vp()
+    _check(_lib.srk_server_create(arr, len(graphs), int(mem_budget), int(n_workers),
+                                  float(latency_target_ms), ctypes.byref(h)))
+    return Server(h.value, graphs)
+
+
+def srk_server_submit(srv: Server, graph: int, s: int, c: float, eps: float, seed: int,
+                      host_scores=None, tag: int = 0) -> bool:
+    """Submit one query; returns whether it was admitted.  ``host_scores``
+    (numpy float64, n) is kept alive by the server object until close()."""
+    hp = None
+    if host_scores is not None:
+        hp, dev, keep = _ptr(host_scores, "float64")
+        if dev:
+            raise ValueError("host_scores must be host memory")
+        srv._buffers.append(keep)
+    adm = ctypes.c_int32()
+    _check(_lib.srk_server_submit(srv.handle, int(graph), int(s), float(c), float(eps),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, hp, int(tag),
+                                  ctypes.byref(adm)))
+    return bool(adm.value)
+
+
+def srk_server_drain(srv: Server) -> None:
+    _check(_lib.srk_server_drain(srv.handle))
+
+
+def srk_server_stats(srv: Server) -> "SrkServerReport":
+    st = SrkServerReport()
+    _check(_lib.srk_server_stats(srv.handle, ctypes.byref(st)))
+    return st
+
+
+def srk_server_destroy(srv: Server) -> None:
+    srv.close()

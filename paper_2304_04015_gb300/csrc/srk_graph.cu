@@ -91,6 +91,7 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
   if (!(c > 0.0 && c < 1.0)) return fail(SRK_EINVAL, "c = %g outside (0, 1)", c);
   double p = 1.0, q = 1.0, z_ovr = 0.0;
   int32_t L_ovr = -1;
+  const bool warmup = opt && (opt->flags & SRK_OPT_WARMUP_RULE);
   if (opt) {
     if (opt->p != 0.0) p = opt->p;
     if (opt->q != 0.0) q = opt->q;
@@ -104,6 +105,9 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
   if (z_ovr > 0.0) {
     if (!isfinite(z_ovr)) return fail(SRK_EINVAL, "z_override is not finite");
     z = z_ovr;
+  } else if (warmup) {  // Section 3: N = ln(2 n^2) / (2 eps^2)
+    if (!(eps > 0.0 && eps < 1.0)) return fail(SRK_EINVAL, "eps = %g outside (0, 1)", eps);
+    z = log(2.0 * (double)n * (double)n) / (2.0 * eps * eps);
   } else {
     const double thr = 3.0 / pow((double)n, p);
     if (!(eps > thr && eps < 1.0))
@@ -114,6 +118,12 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
   int L;
   if (L_ovr >= 0) {
     L = L_ovr;
+  } else if (warmup) {  // Section 3: walks of length >= 3 log_{1/sqrt c}(n/eps) are dropped
+    if (!(eps > 0.0 && eps < 1.0)) return fail(SRK_EINVAL, "eps = %g outside (0, 1)", eps);
+    const double Lf = floor(3.0 * log((double)n / eps) / (-log(rc)));
+    if (!(Lf <= (double)SRK_MAX_LEN))
+      return fail(SRK_EINVAL, "truncation length %g exceeds %d", Lf, SRK_MAX_LEN);
+    L = (int)Lf;
   } else {
     const double Lf = floor(p * log((double)n) / (-log(rc)));
     if (!(Lf <= (double)SRK_MAX_LEN))

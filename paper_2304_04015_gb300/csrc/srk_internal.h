@@ -100,8 +100,11 @@ size_t plan(const QueryTab &t, Workspace *w, char *base);
 // Enqueues steps a2-a5 on `st`; `timing` (may be null) gets two events
 // recorded around the target-walk kernel.
 int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
-                  const Outputs &o, cudaStream_t st,
-                  const cudaEvent_t *timing = nullptr);
+                  const Outputs &o, cudaStream_t st, const cudaEvent_t *timing,
+                  int32_t u_begin, int32_t u_end);
+// [*b, *e): the targets a query computes, from its options (SRK_EINVAL when
+// the range is malformed).
+int target_range(const srk_graph *g, const srk_opts *opt, int32_t *b, int32_t *e);
 // Exclusive scan of cnt[0..N) into off[0..N] (one block of 1024 threads).
 __global__ void k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off,
                        int32_t N);

@@ -60,10 +60,14 @@ extern "C" int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c
   clear_error();
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (!scores) return fail(SRK_EINVAL, "scores is null");
-  if (opt && opt->flags != 0) return fail(SRK_EINVAL, "opts.flags must be 0");
+  if (opt && (opt->flags & ~SRK_OPT_WARMUP_RULE))
+    return fail(SRK_EINVAL, "unsupported opts.flags 0x%x", opt->flags);
   uint32_t *step_counts = opt ? opt->step_counts : nullptr;
   QueryTab t;
   int rc = build_table(g->n, s, c, eps, seed, opt, &t);
+  if (rc) return rc;
+  int32_t u_begin = 0, u_end = g->n;
+  rc = target_range(g, opt, &u_begin, &u_end);
   if (rc) return rc;
   DeviceGuard guard(g->device);
   // host outputs would need a device staging buffer: only device memory here
@@ -89,7 +93,7 @@ extern "C" int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c
   o.steps = step_counts;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   rc = enqueue_query(g, t, w, o, st,
-                     opt ? (const cudaEvent_t *)opt->timing_events : nullptr);
+                     opt ? (const cudaEvent_t *)opt->timing_events : nullptr, u_begin, u_end);
   if (!rc && opt && opt->stats) rc = read_stats(t, w, st, opt->stats, false);
   return rc;
 }

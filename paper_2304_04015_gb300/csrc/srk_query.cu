@@ -267,6 +267,7 @@ struct TargetArgs {
   uint32_t *steps_per_target;
   unsigned long long *steps_total;
   int32_t *target_counter;  // zeroed before the launch
+  int32_t u_begin, u_end;   // targets computed: [u_begin, u_end)
 };
 
 // 8 blocks of 256 threads per SM (32 registers): the kernel is bound by the
@@ -299,9 +300,9 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
   unsigned long long warp_steps = 0;
   for (;;) {
     int32_t u = 0;
-    if (lane == 0) u = atomicAdd(A.target_counter, 1);
+    if (lane == 0) u = A.u_begin + atomicAdd(A.target_counter, 1);
     u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= A.n) break;
+    if (u >= A.u_end) break;
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
     const int32_t beg_u = u + A.row_ptr[u];  // position of u
@@ -383,7 +384,8 @@ static int target_grid(int device) {
 // Enqueues one query on `st` with device-resident outputs `o`.  Workspace
 // `w` (already carved) must hold plan(t) bytes.
 int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
-                  const Outputs &o, cudaStream_t st, const cudaEvent_t *timing) {
+                  const Outputs &o, cudaStream_t st, const cudaEvent_t *timing,
+                  int32_t u_begin, int32_t u_end) {
   const int dev = g->device;
   const int N = t.N_tot;
   const int gN = grid_for(N, 256, dev);
@@ -419,11 +421,28 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.steps_per_target = o.steps;
   A.steps_total = small_view(w.small).ctr;
   A.target_counter = reinterpret_cast<int32_t *>(small_view(w.small).ctr + 2);
+  A.u_begin = u_begin;
+  A.u_end = u_end;
   if (timing) cudaEventRecord(timing[0], st);
   k_target_walks<<<target_grid(dev), 256, 0, st>>>(A);
   if (timing) cudaEventRecord(timing[1], st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return SRK_OK;
+}
+
+// The target range of a query from its options: [0, n) by default.
+int target_range(const srk_graph *g, const srk_opts *opt, int32_t *b, int32_t *e) {
+  *b = 0;
+  *e = g->n;
+  if (opt && (opt->target_begin != 0 || opt->target_end != 0)) {
+    if (opt->target_begin < 0 || opt->target_begin > opt->target_end ||
+        opt->target_end > g->n)
+      return fail(SRK_EINVAL, "target range [%d, %d) outside [0, %d]", opt->target_begin,
+                  opt->target_end, g->n);
+    *b = opt->target_begin;
+    *e = opt->target_end;
+  }
   return SRK_OK;
 }
 
@@ -463,9 +482,13 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
   clear_error();
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (!scores) return fail(SRK_EINVAL, "scores is null");
-  if (opt && opt->flags != 0) return fail(SRK_EINVAL, "opts.flags must be 0");
+  if (opt && (opt->flags & ~SRK_OPT_WARMUP_RULE))
+    return fail(SRK_EINVAL, "unsupported opts.flags 0x%x", opt->flags);
   QueryTab t;
   int rc = build_table(g->n, s, c, eps, seed, opt, &t);
+  if (rc) return rc;
+  int32_t u_begin = 0, u_end = g->n;
+  rc = target_range(g, opt, &u_begin, &u_end);
   if (rc) return rc;
   DeviceGuard guard(g->device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -500,16 +523,18 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
                     : (unsigned long long *)(base + o_wsums);
   o.steps = d_steps ? step_counts : (uint32_t *)(base + o_steps);
   rc = enqueue_query(g, t, w, o, st,
-                     opt ? (const cudaEvent_t *)opt->timing_events : nullptr);
+                     opt ? (const cudaEvent_t *)opt->timing_events : nullptr, u_begin, u_end);
   bool host_out = !d_scores || !d_counts || !d_wsums || !d_steps;
-  if (!rc) {
-    if (!d_scores) e = cudaMemcpyAsync(scores, o.scores, 8 * n, cudaMemcpyDeviceToHost, st);
+  if (!rc) {  // host outputs: copy back the computed range only
+    const size_t b = (size_t)u_begin, cnt = (size_t)(u_end - u_begin);
+    if (!d_scores)
+      e = cudaMemcpyAsync(scores + b, o.scores + b, 8 * cnt, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && !d_counts)
-      e = cudaMemcpyAsync(meet_counts, o.counts, 4 * n, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(meet_counts + b, o.counts + b, 4 * cnt, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && !d_wsums)
-      e = cudaMemcpyAsync(weight_sums, o.wsums, 8 * n, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(weight_sums + b, o.wsums + b, 8 * cnt, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && !d_steps)
-      e = cudaMemcpyAsync(step_counts, o.steps, 4 * n, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(step_counts + b, o.steps + b, 4 * cnt, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "copying results to the host");
   }
   if (!rc && opt && opt->stats) rc = read_stats(t, w, st, opt->stats, false);

@@ -317,3 +317,45 @@ def test_batched_many_batches_graph_and_host_outputs(srk, monkeypatch):
     for i in (0, 7, len(sources) - 1):
         one = gpu_query(srk, rp, col, sources[i], eps[i], 5)
         assert np.array_equal(one[0], a[0][i]) and np.array_equal(one[1], a[1][i])
+
+
+def test_target_ranges_compose_the_full_query(srk):
+    # the owner rule: slices [b, e) computed separately (device and host
+    # outputs) equal the full query and leave everything else untouched
+    import torch
+    rp, col = rmat_graph(16)
+    n = rp.size - 1
+    full = gpu_query(srk, rp, col, 4242, 0.05, 31)
+    dev = torch.device("cuda:0")
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        cuts = [0, n // 3, n // 3 + 1, 2 * n // 3, n]
+        sc = torch.full((n,), -7.0, dtype=torch.float64, device=dev)
+        cnt_h = np.full(n, 12345, dtype=np.uint32)
+        total = 0
+        for b, e in zip(cuts[:-1], cuts[1:]):
+            st = srk.SrkStats()
+            srk.srk_single_source(g, 4242, C, 0.05, 31, sc, cnt_h, stats=st, target_range=(b, e))
+            total += st.target_steps
+        torch.cuda.synchronize()
+        assert np.array_equal(sc.cpu().numpy(), full[0])
+        assert np.array_equal(cnt_h, full[1])
+        assert total == full[4].target_steps
+        part = np.full(n, 3, dtype=np.uint32)
+        sc2 = np.full(n, -1.0)
+        srk.srk_single_source(g, 4242, C, 0.05, 31, sc2, part, target_range=(100, 200))
+        assert np.all(part[:100] == 3) and np.all(part[200:] == 3)
+        assert np.array_equal(part[100:200], full[1][100:200])
+        assert np.all(sc2[:100] == -1.0) and np.array_equal(sc2[100:200], full[0][100:200])
+        with pytest.raises(srk.SrkError):
+            srk.srk_single_source(g, 0, C, 0.05, 1, sc, target_range=(5, n + 1))
+    finally:
+        g.close()
+
+
+def test_warmup_rule_bit_exact(srk):
+    rp, col = er_graph(200, 3.0, 4)
+    gpu = gpu_query(srk, rp, col, 3, 0.3, 12, warmup_rule=True)
+    ref = oracle_query(rp, col, 3, 0.3, 12, warmup_rule=True)
+    assert_parity(gpu, ref)
+    assert gpu[4].L == ref.table.L > 0

@@ -91,3 +91,16 @@ def test_rejects_bad_c():
     for c in (0.0, 1.0, -0.1, 1.5):
         with pytest.raises(ValueError):
             sample_table(1000, c, 0.1)
+
+
+def test_warmup_rule_sample_size_and_truncation():
+    # Section 3: N = ln(2 n^2) / (2 eps^2) gives 2 exp(-2 N eps^2) = 1/n^2, and a
+    # walk reaches length 3 log_{1/sqrt c}(n/eps) with probability (eps/n)^3
+    n, eps, c = 1000, 0.1, 0.6
+    tab = sample_table(n, c, eps, warmup_rule=True)
+    assert 2.0 * math.exp(-2.0 * tab.z * eps * eps) == pytest.approx(1.0 / n ** 2, rel=1e-12)
+    rc = math.sqrt(c)
+    assert rc ** tab.L >= (eps / n) ** 3 * (1 - 1e-12)
+    assert rc ** (tab.L + 1) < (eps / n) ** 3
+    with pytest.raises(ValueError):
+        sample_table(n, c, 1.2, warmup_rule=True)
