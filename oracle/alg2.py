@@ -35,7 +35,10 @@ def tuples_of_walk(j: int, walk_nodes, length: int, v0: int):
 
 
 def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
-        z_override=None, L_override=None):
+        z_override=None, L_override=None, literal_shuffle=False):
+    """``literal_shuffle``: every target's walk r carries the label j with
+    pi_u(j) = r (the keyed per-target permutation), as the paper shuffles
+    every node's walks."""
     tab = sample_table(n, c, eps, z_override=z_override, L_override=L_override)
     L, N_tot = tab.L, tab.N_tot
     lengths = np.array([tab.stratum(r) for r in range(N_tot)], dtype=np.int64)
@@ -46,11 +49,19 @@ def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
     J, I, V, T, V0 = [], [], [], [], []
     for v0 in range(n):
         pos, eff = sampler.walks(row_ptr, col, v0, s, seed, tab)
+        inv_u = None
+        if literal_shuffle and v0 != s:
+            inv_u = np.empty(N_tot, dtype=np.int64)
+            for j in range(N_tot):
+                inv_u[sampler.feistel(v0, s, seed, N_tot, j)] = j
         for r in range(N_tot):
             e = int(eff[r])
             if e == 0:
                 continue
-            label = int(inv[r]) if v0 == s else r
+            if v0 == s:
+                label = int(inv[r])
+            else:
+                label = int(inv_u[r]) if inv_u is not None else r
             J.append(np.full(e, label))
             I.append(np.arange(1, e + 1))
             V.append(pos[r, :e].astype(np.int64))

@@ -31,6 +31,15 @@
  *   Fisher-Yates draw t: counter = (t >> 1, 0xFFFFFFFF, 0xFFFFFFFF, s),
  *           words 2*(t&1) (high) and 2*(t&1)+1 (low)
  *   uniform index below d from a 64-bit draw R: floor(R * d / 2^64).
+ *
+ * Optional literal shuffle of the targets' walks (every node's walks are
+ * shuffled in Section 5.2; the default shuffles only the source's): target u
+ * pairs walk pi_u(j) with source walk sigma[j], where pi_u is a keyed
+ * permutation of 0..N_tot-1: a 4-round Feistel network on b bits (b the
+ * smallest even number >= 2 with 2^b >= N_tot, halves of h = b/2 bits) with
+ * round function F_r(x) = word 0 of Philox(counter (x, 0xFFFFFFF0 + r, u, s))
+ * masked to h bits, (L, R) -> (R, L ^ F_r(R)) for r = 0..3, repeated on its
+ * own output until the value falls below N_tot (cycle walking).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -93,6 +102,29 @@ int srko_walk(const int32_t *row_ptr, const int32_t *col, int32_t v,
     return len;
 }
 
+/* pi_u(j): the keyed permutation of the literal target shuffle (see above). */
+int32_t srko_feistel(int32_t u, int32_t s, uint64_t seed, int32_t N, int32_t j) {
+    int b = 2;
+    while (((int64_t)1 << b) < (int64_t)N) b += 2;
+    const int h = b / 2;
+    const uint32_t mask = ((uint32_t)1 << h) - 1u;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t v = (uint32_t)j;
+    do {
+        uint32_t Lh = v >> h, Rh = v & mask;
+        for (uint32_t r = 0; r < 4; ++r) {
+            uint32_t ctr[4] = {Rh, 0xFFFFFFF0u + r, (uint32_t)u, (uint32_t)s};
+            uint32_t w[4];
+            srko_philox4x32_10(ctr, key, w);
+            uint32_t t = Lh ^ (w[0] & mask);
+            Lh = Rh;
+            Rh = t;
+        }
+        v = (Lh << h) | Rh;
+    } while (v >= (uint32_t)N);
+    return (int32_t)v;
+}
+
 static int stratum_of(const int32_t *P, int L, int32_t r) {
     int lo = 0, hi = L;
     while (lo < hi) {
@@ -135,6 +167,7 @@ void srko_fisher_yates(int32_t s, uint64_t seed, int32_t N_tot,
 
 /*
  * Steps a2-a4 for query source s and the targets listed in `targets`
+ * (literal != 0: target walks are paired through pi_u, see above)
  * (n_targets entries; any node ids, s included).  wq is the (L+1)x(L+1)
  * quantised weight table, row l1 (source length), column l2 (target length).
  * Outputs per listed target: meet count, weight sum (2^-32 units) and the
@@ -146,7 +179,8 @@ int srko_sampler(const int32_t *row_ptr, const int32_t *col, int32_t n,
                  int32_t s, uint64_t seed, int L, const int32_t *P,
                  const uint64_t *wq, const int32_t *targets,
                  int64_t n_targets, uint32_t *count, uint64_t *wsum,
-                 uint64_t *steps, uint64_t *source_steps, int threads) {
+                 uint64_t *steps, uint64_t *source_steps, int threads,
+                 int literal) {
     (void)n;
     int stride = L > 0 ? L : 1;
     int32_t N_tot = P[L + 1];
@@ -190,10 +224,12 @@ int srko_sampler(const int32_t *row_ptr, const int32_t *col, int32_t n,
             if (tpos && u != s) {
                 for (int32_t j = 0; j < N_tot; ++j) {
                     /* a4: pair j = (source walk sigma[j], target walk j) */
-                    int l2 = stratum_of(P, L, j);
+                    /* target walk paired with source walk sigma[j] */
+                    int32_t tw = literal ? srko_feistel(u, s, seed, N_tot, j) : j;
+                    int l2 = stratum_of(P, L, tw);
                     int32_t w = sigma[j];
                     int l1 = stratum_of(P, L, w);
-                    int teff = srko_walk(row_ptr, col, u, j, s, seed, l2, tpos);
+                    int teff = srko_walk(row_ptr, col, u, tw, s, seed, l2, tpos);
                     int m = teff < seff[w] ? teff : seff[w];
                     const int32_t *sp = spos + (int64_t)w * stride;
                     int met = 0;

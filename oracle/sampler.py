@@ -58,8 +58,11 @@ def lib():
         L.srko_sampler.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_uint64, ctypes.c_int, i32p, u64p,
                                    i32p, ctypes.c_int64, u32p, u64p, u64p, u64p,
-                                   ctypes.c_int]
+                                   ctypes.c_int, ctypes.c_int]
         L.srko_sampler.restype = ctypes.c_int
+        L.srko_feistel.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.c_int32, ctypes.c_int32]
+        L.srko_feistel.restype = ctypes.c_int32
         _lib = L
     return _lib
 
@@ -105,6 +108,11 @@ def walks(row_ptr, col, v: int, s: int, seed: int, tab: Table):
     return pos, eff
 
 
+def feistel(u: int, s: int, seed: int, N: int, j: int) -> int:
+    """pi_u(j) of the literal target shuffle."""
+    return int(lib().srko_feistel(u, s, ctypes.c_uint64(seed), N, j))
+
+
 def fisher_yates(s: int, seed: int, N_tot: int) -> np.ndarray:
     sigma = np.empty(N_tot, dtype=np.int32)
     lib().srko_fisher_yates(s, ctypes.c_uint64(seed), N_tot,
@@ -135,8 +143,10 @@ class Result:
 
 def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
         targets=None, z_override=None, L_override=None, p: float = 1.0,
-        q: float = 1.0, warmup_rule: bool = False, threads: int = 0) -> Result:
-    """One single-source query, steps a1-a5, for ``targets`` (all nodes if None)."""
+        q: float = 1.0, warmup_rule: bool = False, literal_shuffle: bool = False,
+        threads: int = 0) -> Result:
+    """One single-source query, steps a1-a5, for ``targets`` (all nodes if None).
+    ``literal_shuffle``: also shuffle every target's walks (by pi_u)."""
     tab = sample_table(n, c, eps, p=p, q=q, z_override=z_override,
                        L_override=L_override, warmup_rule=warmup_rule)
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -158,7 +168,8 @@ def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
                             _ptr(count, ctypes.c_uint32),
                             _ptr(wsum, ctypes.c_uint64),
                             _ptr(steps, ctypes.c_uint64),
-                            _ptr(src_steps, ctypes.c_uint64), threads)
+                            _ptr(src_steps, ctypes.c_uint64), threads,
+                            1 if literal_shuffle else 0)
     if rc != 0:
         raise MemoryError("oracle sampler ran out of memory")
     # a5: s~(s, u) = W_u 2^-32 / z; s~(s, s) = 1

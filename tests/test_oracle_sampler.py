@@ -122,3 +122,44 @@ def test_step_totals_against_plain_rewalk():
                     break
             steps += taken
         assert r.steps[u] == steps
+
+
+def test_literal_shuffle_permutation_and_marginal():
+    for N in (1, 2, 3, 7, 64, 65, 1000, 2018):
+        perm = [sampler.feistel(11, 2, 5, N, j) for j in range(N)]
+        assert sorted(perm) == list(range(N))
+    # pi_u(j) for a fixed j is uniform over targets u (chi-square, 9 dof)
+    N, trials = 10, 5000
+    counts = np.bincount([sampler.feistel(u, 3, 77, N, 4) for u in range(trials)], minlength=N)
+    exp = trials / N
+    assert float(((counts - exp) ** 2 / exp).sum()) < 35.0
+
+
+@pytest.mark.parametrize("n,deg,s,seed", [(60, 3.0, 0, 11), (50, 2.0, 9, 4)])
+def test_literal_shuffle_algorithm2_equals_direct(n, deg, s, seed):
+    rp, col = er_in_csr(n, deg, seed=seed)
+    r = sampler.run(rp, col, n, s, C, 0.5, seed, z_override=200.0, literal_shuffle=True)
+    cnt, ws = alg2.run(rp, col, n, s, C, 0.5, seed, z_override=200.0, literal_shuffle=True)
+    assert np.array_equal(r.count, cnt) and np.array_equal(r.wsum, ws)
+    plain = sampler.run(rp, col, n, s, C, 0.5, seed, z_override=200.0)
+    assert not np.array_equal(plain.count, r.count)
+
+
+def test_literal_shuffle_mean_matches_exact_expectation():
+    # shuffling the targets' walks too leaves each target's law unchanged
+    n, s = 120, 0
+    rp, col = er_in_csr(n, 2.0, seed=21)
+    tab = sample_table(n, C, 0.5, z_override=300.0, L_override=15)
+    F = exact.first_meeting(rp, col, n, tab.L, rows=[s])[:, 0, :]
+    expect = exact.estimator_expectation(F, tab, quantised=True)
+    seeds = 300
+    acc = np.zeros((seeds, n))
+    for k in range(seeds):
+        acc[k] = sampler.run(rp, col, n, s, C, 0.5, 5000 + k, z_override=300.0,
+                             L_override=15, literal_shuffle=True).scores
+    acc[:, s] = 0.0
+    expect[s] = 0.0
+    mean, sd = acc.mean(axis=0), acc.std(axis=0, ddof=1)
+    live = sd > 0
+    z = np.abs(mean[live] - expect[live]) / (sd[live] / np.sqrt(seeds))
+    assert live.sum() > 10 and z.max() < 5.0
