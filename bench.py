@@ -193,17 +193,24 @@ def gather_probe(srk, torch, dev, n_words):
     return rate
 
 
+def kernel_source_sha256():
+    """sha256 over the sources the target-walk kernel is compiled from (the
+    kernel file, then the device header), in that order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("srk_query.cu", "srk_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2304_04015_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def recorded_traffic():
     """DRAM bytes per target-walk step of the target-walk kernel, from the
-    committed ncu summary, if it was taken on the current kernel source."""
-    import hashlib
+    committed ncu summary, if it was taken on the current kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_target_walks_rmat20_traffic.json")) as f:
             rec = json.load(f)
-        src = os.path.join(ROOT, "paper_2304_04015_gb300", "csrc", "srk_query.cu")
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        if rec.get("srk_query_cu_sha256") != sha:
+        if rec.get("kernel_sources_sha256") != kernel_source_sha256():
             return None
         return float(rec["dram_bytes_per_launch"]) / float(rec["target_steps_of_launch"])
     except Exception:

@@ -61,6 +61,12 @@ extern "C" {
                                   (Section 3): z = ln(2 n^2) / (2 eps^2),
                                   L = floor(3 ln(n / eps) / ln(1/sqrt c));
                                   p and q are then not used */
+#define SRK_OPT_LITERAL_SHUFFLE 4  /* single-source only: shuffle every
+                                  target's walks too, by a keyed per-target
+                                  permutation (4-round Feistel, Philox round
+                                  functions), as Section 5.2 shuffles every
+                                  node's walks; slower (about 4 extra Philox
+                                  blocks per pair) */
 
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */
@@ -155,7 +161,7 @@ int srk_graph_info(const srk_graph *g, int32_t *n, int64_t *m);
  * with target walk j.  A pair meets when both walks are at the same node at
  * the same step i >= 1; it counts once.  A walk stops early at a node without
  * in-neighbours.  Returns SRK_EINVAL for s, c, eps, p, q out of range, or
- * when L > SRK_MAX_LEN or N_tot > SRK_MAX_WALKS.
+ * when L > SRK_MAX_LEN, N_tot > SRK_MAX_WALKS or sum_l l N_l >= 2^31.
  */
 int srk_single_source(const srk_graph *g, int32_t s, double c, double eps,
                       uint64_t seed, const srk_opts *opt, double *scores,

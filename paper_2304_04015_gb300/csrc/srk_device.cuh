@@ -269,3 +269,119 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const Adj &G,
 }
 
 }  // namespace srk
+
+namespace srk {
+
+// ---------------------------------------------------------------------------
+// Literal target shuffle: target u pairs its walk pi_u(j) with source walk
+// sigma[j].  pi_u is a 4-round Feistel network on b bits (b the smallest even
+// number >= 2 with 2^b >= N, halves of h = b/2 bits), round function
+// F_r(x) = word 0 of Philox(counter (x, 0xFFFFFFF0 + r, u, s)) masked to h
+// bits, (L, R) -> (R, L ^ F_r(R)), applied again until the value is below N
+// (cycle walking; the orbit of j < N returns below N within 2^b steps).
+struct FeistelShape {
+  int h;          // bits per half
+  uint32_t mask;  // 2^h - 1
+  int32_t N;
+};
+
+__host__ __device__ __forceinline__ FeistelShape feistel_shape(int32_t N) {
+  int b = 2;
+  while (((int64_t)1 << b) < (int64_t)N) b += 2;
+  FeistelShape f;
+  f.h = b / 2;
+  f.mask = (1u << f.h) - 1u;
+  f.N = N;
+  return f;
+}
+
+__device__ __forceinline__ int32_t feistel_pi(const RoundKeys &rk, const FeistelShape &f,
+                                              uint32_t u, uint32_t s, int32_t j) {
+  uint32_t v = (uint32_t)j;
+  const uint32_t limit = 1u << (2 * f.h);
+  for (uint32_t guard = 0; guard < limit; ++guard) {
+    uint32_t Lh = v >> f.h, Rh = v & f.mask;
+#pragma unroll 1
+    for (uint32_t r = 0; r < 4; ++r) {
+      uint32_t x0, x1, x2, x3;
+      philox(rk, Rh, 0xFFFFFFF0u + r, u, s, x0, x1, x2, x3);
+      const uint32_t t = Lh ^ (x0 & f.mask);
+      Lh = Rh;
+      Rh = t;
+    }
+    v = (Lh << f.h) | Rh;
+    if (v < (uint32_t)f.N) break;
+  }
+  return (int32_t)v;
+}
+
+// walk_target in the literal mode: pair a (index j, source length l1 stored
+// in pair_w[a]) walks target walk t = pi_u(j) of length l2 = stratum(t),
+// Philox replica t; it ends after min(l2, source cap) steps; a meeting adds
+// round(a(l1) a(l2) 2^32).  P (stratum prefix, shared memory) and a (Lemma 7
+// weights) come from the query table.
+__device__ __forceinline__ void walk_target_literal(
+    const RoundKeys &rk, const Adj &G, const PairSet &S, const FeistelShape &f,
+    const int32_t *P, int L, const double *aw, uint32_t u,
+    int32_t beg_u, uint32_t deg_u, uint32_t lanes_below, uint32_t &c,
+    unsigned long long &W, uint32_t &st) {
+  int32_t next = 0;
+  bool live = false;
+  int32_t a = 0, i = 1, p = 0, l2 = 0;
+  uint32_t deg = 0, t = 0;
+  for (;;) {
+    const uint32_t idle = __ballot_sync(0xffffffffu, !live);
+    if (idle) {
+      if (!live) {
+        a = next + __popc(idle & lanes_below);
+        if (a < S.n_pairs) {
+          t = (uint32_t)feistel_pi(rk, f, u, S.s, S.pair_j[a]);
+          l2 = stratum_of(P, L, (int32_t)t);
+          live = l2 >= 1;  // a length-0 target walk takes no step
+          i = 1;
+          p = beg_u;
+          deg = deg_u;
+        }
+      }
+      next += __popc(idle);
+    }
+    if (!__any_sync(0xffffffffu, live)) break;
+    if (live) {
+      uint32_t x0, x1, x2, x3;
+      philox(rk, (uint32_t)(i - 1) >> 1, t, u, S.s, x0, x1, x2, x3);
+      uint32_t e = adj_entry(G, p, deg, x0, x1);
+      int32_t x = entry_pos(G, e);
+      ++st;
+      if (x == S.Hc[S.R[i] + a]) {
+        ++c;
+        W += __double2ull_rn(aw[(int)S.pair_w[a]] * aw[l2] * 4294967296.0);
+        live = false;
+      } else if (a >= S.cnt[i + 1] || i >= l2) {
+        live = false;
+      } else {
+        deg = entry_deg(G, e, x);
+        if (deg == 0) {
+          live = false;
+        } else {
+          e = adj_entry(G, x, deg, x2, x3);
+          x = entry_pos(G, e);
+          ++st;
+          if (x == S.Hc[S.R[i + 1] + a]) {
+            ++c;
+            W += __double2ull_rn(aw[(int)S.pair_w[a]] * aw[l2] * 4294967296.0);
+            live = false;
+          } else if (a >= S.cnt[i + 2] || i + 1 >= l2) {
+            live = false;
+          } else {
+            deg = entry_deg(G, e, x);
+            if (deg == 0) live = false;
+            p = x;
+            i += 2;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace srk

@@ -137,6 +137,8 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
   t->L = L;
   t->key0 = (uint32_t)seed;
   t->key1 = (uint32_t)(seed >> 32);
+  t->literal = (opt && (opt->flags & SRK_OPT_LITERAL_SHUFFLE)) ? 1 : 0;
+  t->pad_ = 0;
   t->z = z;
   int64_t acc = 0;
   t->P[0] = 0;
@@ -152,6 +154,12 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
     t->P[l + 1] = (int32_t)acc;
   }
   t->N_tot = (int32_t)acc;
+  // the hit table holds at most sum_l l N_l entries, indexed with int32
+  int64_t cells = 0;
+  for (int l = 1; l <= L; ++l) cells += (int64_t)l * (t->P[l + 1] - t->P[l]);
+  if (cells > INT32_MAX)
+    return fail(SRK_EINVAL, "walk budget too large: sum_l l N_l = %lld exceeds 2^31",
+                (long long)cells);
   return SRK_OK;
 }
 

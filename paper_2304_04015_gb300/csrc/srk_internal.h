@@ -40,6 +40,7 @@ namespace srk {
 struct QueryTab {
   int32_t s, n, L, N_tot;
   uint32_t key0, key1;
+  int32_t literal, pad_;  // 1: literal target shuffle (SRK_OPT_LITERAL_SHUFFLE)
   double z;
   int32_t P[SRK_MAX_LEN + 2];  // stratum prefix: walk r has length l iff P[l] <= r < P[l+1]
   double a[SRK_MAX_LEN + 1];   // rounding weight a(l) = |Z_l| / |Z^_l|

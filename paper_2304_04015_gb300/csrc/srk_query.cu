@@ -172,8 +172,8 @@ k_pairs(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ kdraw,
        j += gridDim.x * blockDim.x) {
     const int32_t p = resolve_sigma(j, kdraw, first, succ, N);
     sigma[j] = p;
-    const int l2 = stratum_of(P, tab.L, j);
-    const int32_t cap = min(l2, seff[p]);
+    // literal mode: the target walk is pi_u(j), so only the source bounds the cap
+    const int32_t cap = tab.literal ? seff[p] : min(stratum_of(P, tab.L, j), seff[p]);
     if (cap >= 1) atomicAdd(&hist[cap], 1);
   }
   __syncthreads();
@@ -224,12 +224,14 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
        j += gridDim.x * blockDim.x) {
     const int32_t w = sigma[j];
     const int l2 = stratum_of(P, tab.L, j);
-    const int32_t cap = min(l2, seff[w]);
+    const int32_t cap = tab.literal ? seff[w] : min(l2, seff[w]);
     if (cap < 1) continue;
     const int l1 = stratum_of(P, tab.L, w);
     const int32_t a = atomicAdd(&sm.cursor[cap], 1);
     pair_j[a] = j;
-    pair_w[a] = __double2ull_rn(tab.a[l1] * tab.a[l2] * 4294967296.0);
+    // literal mode keeps l1: the weight needs the target walk's length
+    pair_w[a] = tab.literal ? (unsigned long long)l1
+                            : __double2ull_rn(tab.a[l1] * tab.a[l2] * 4294967296.0);
     const int32_t *src = spos + (int64_t)w * Ls;
     for (int i = 1; i <= cap; ++i) Hc[R[i] + a] = src[i - 1];
   }
@@ -268,20 +270,30 @@ struct TargetArgs {
   unsigned long long *steps_total;
   int32_t *target_counter;  // zeroed before the launch
   int32_t u_begin, u_end;   // targets computed: [u_begin, u_end)
+  int32_t N_tot;            // literal mode: the permutation's domain
+};
+
+// Literal mode also needs the stratum prefix and the Lemma 7 weights.
+struct LiteralArgs {
+  int32_t P[SRK_MAX_LEN + 2];
+  double a[SRK_MAX_LEN + 1];
 };
 
 // 8 blocks of 256 threads per SM (32 registers): the kernel is bound by the
 // rate of scattered L1 misses, and full occupancy keeps the most misses in
-// flight.
+// flight.  kLiteral: the literal target shuffle (walk_target_literal).
+template <bool kLiteral>
 __global__ void __launch_bounds__(256, 8)
-k_target_walks(const __grid_constant__ TargetArgs A) {
+k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ LiteralArgs X) {
   __shared__ int32_t cnt[SRK_MAX_LEN + 3];
   __shared__ int32_t R[SRK_MAX_LEN + 3];
+  __shared__ int32_t Psh[kLiteral ? SRK_MAX_LEN + 2 : 1];
   {
     const Small sm = small_view(const_cast<int32_t *>(A.small_base));
     for (int i = threadIdx.x; i <= A.L + 2; i += blockDim.x) {
       cnt[i] = (i <= A.L + 1) ? sm.cnt[i] : 0;  // cnt[L+1] = cnt[L+2] = 0
       R[i] = (i <= A.L + 1) ? sm.R[i] : 0;
+      if (kLiteral && i <= A.L + 1) Psh[i] = X.P[i];
     }
   }
   __syncthreads();
@@ -297,6 +309,7 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
   S.Hc = A.Hc;
   S.n_pairs = cnt[1];
   S.s = (uint32_t)A.s;
+  const FeistelShape fs = feistel_shape(A.N_tot);
   unsigned long long warp_steps = 0;
   for (;;) {
     int32_t u = 0;
@@ -307,8 +320,13 @@ k_target_walks(const __grid_constant__ TargetArgs A) {
     unsigned long long W = 0;
     const int32_t beg_u = u + A.row_ptr[u];  // position of u
     const uint32_t deg_u = G.adj[beg_u];
-    if (u != A.s && deg_u > 0)
-      walk_target(rk, G, S, (uint32_t)u, beg_u, deg_u, lanes_below, c, W, st);
+    if (u != A.s && deg_u > 0) {
+      if (kLiteral)
+        walk_target_literal(rk, G, S, fs, Psh, A.L, X.a, (uint32_t)u, beg_u, deg_u,
+                            lanes_below, c, W, st);
+      else
+        walk_target(rk, G, S, (uint32_t)u, beg_u, deg_u, lanes_below, c, W, st);
+    }
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
       st += __shfl_xor_sync(0xffffffffu, st, off);
@@ -371,7 +389,7 @@ static int target_grid(int device) {
   static int blocks_per_sm[64] = {};
   int b = (device >= 0 && device < 64) ? blocks_per_sm[device] : 0;
   if (!b) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks, 256, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks<false>, 256, 0) !=
             cudaSuccess || b < 1)
       b = 1;
     if (device >= 0 && device < 64) blocks_per_sm[device] = b;
@@ -423,8 +441,19 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.target_counter = reinterpret_cast<int32_t *>(small_view(w.small).ctr + 2);
   A.u_begin = u_begin;
   A.u_end = u_end;
+  A.N_tot = t.N_tot;
+  LiteralArgs X;
+  if (t.literal) {
+    memcpy(X.P, t.P, sizeof X.P);
+    memcpy(X.a, t.a, sizeof X.a);
+  } else {
+    memset(&X, 0, sizeof X);
+  }
   if (timing) cudaEventRecord(timing[0], st);
-  k_target_walks<<<target_grid(dev), 256, 0, st>>>(A);
+  if (t.literal)
+    k_target_walks<true><<<target_grid(dev), 256, 0, st>>>(A, X);
+  else
+    k_target_walks<false><<<target_grid(dev), 256, 0, st>>>(A, X);
   if (timing) cudaEventRecord(timing[1], st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -482,7 +511,7 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
   clear_error();
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (!scores) return fail(SRK_EINVAL, "scores is null");
-  if (opt && (opt->flags & ~SRK_OPT_WARMUP_RULE))
+  if (opt && (opt->flags & ~(SRK_OPT_WARMUP_RULE | SRK_OPT_LITERAL_SHUFFLE)))
     return fail(SRK_EINVAL, "unsupported opts.flags 0x%x", opt->flags);
   QueryTab t;
   int rc = build_table(g->n, s, c, eps, seed, opt, &t);

@@ -359,3 +359,45 @@ def test_warmup_rule_bit_exact(srk):
     ref = oracle_query(rp, col, 3, 0.3, 12, warmup_rule=True)
     assert_parity(gpu, ref)
     assert gpu[4].L == ref.table.L > 0
+
+
+@pytest.mark.parametrize("z,L", [(2000.0, 32), (1.0, 0), (37.0, 5)])
+def test_literal_shuffle_bit_exact(srk, z, L):
+    # every target's walks shuffled by its own keyed permutation (Section 4.2
+    # read literally): Feistel domains of 4, 64 and 4096 with cycle walking
+    rp, col = er_graph(1000, 5.0, 1)
+    for s, seed in ((0, 1), (17, 9)):
+        gpu = gpu_query(srk, rp, col, s, 0.1, seed, z_override=z, L_override=L,
+                        literal_shuffle=True)
+        ref = oracle_query(rp, col, s, 0.1, seed, z_override=z, L_override=L,
+                           literal_shuffle=True)
+        assert_parity(gpu, ref)
+    plain = gpu_query(srk, rp, col, 0, 0.1, 1, z_override=2000.0, L_override=32)
+    lit = gpu_query(srk, rp, col, 0, 0.1, 1, z_override=2000.0, L_override=32,
+                    literal_shuffle=True)
+    assert not np.array_equal(plain[1], lit[1])
+
+
+def test_literal_shuffle_rmat_sampled_targets_and_ranges(srk):
+    rp, col = rmat_graph(14)
+    n = rp.size - 1
+    rng = np.random.default_rng(3)
+    targets = np.sort(rng.choice(n, 300, replace=False)).astype(np.int64)
+    gpu = gpu_query(srk, rp, col, 99, 0.1, 4, literal_shuffle=True, device_outputs=False)
+    ref = oracle_query(rp, col, 99, 0.1, 4, targets=targets, literal_shuffle=True)
+    assert_parity(gpu, ref, targets)
+    import torch
+    dev = torch.device("cuda:0")
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        part = np.zeros(n, dtype=np.uint32)
+        for b, e in ((0, n // 2), (n // 2, n)):
+            srk.srk_single_source(g, 99, C, 0.1, 4, np.empty(n), part,
+                                  target_range=(b, e), literal_shuffle=True)
+        assert np.array_equal(part, gpu[1])
+        with pytest.raises(srk.SrkError):
+            srk.srk_multi_source(g, [1, 2], C, [0.1, 0.1], 4,
+                                 torch.empty((2, n), dtype=torch.float64, device=dev),
+                                 literal_shuffle=True)
+    finally:
+        g.close()

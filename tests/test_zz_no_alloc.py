@@ -42,7 +42,9 @@ def test_no_alloc_matches_allocating_entry_point(srk):
     cases = []
     rp, col = er_in_csr(1000, 5.0, seed=1)
     cases.append((rp, col, [(0, 0.1, 1, dict(z_override=2000.0, L_override=32)),
-                            (17, 0.1, 2, dict(z_override=2000.0, L_override=32))]))
+                            (17, 0.1, 2, dict(z_override=2000.0, L_override=32)),
+                            (5, 0.1, 3, dict(z_override=2000.0, L_override=32,
+                                             literal_shuffle=True))]))
     rp16, col16 = rmat_in_csr(16, seed=1)
     hub = int(np.argmax(np.diff(rp16)))
     cases.append((rp16, col16, [(hub, 0.05, 3, {}), (12345, 0.05, 4, {})]))
