@@ -209,7 +209,11 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
  *   s_out  : n FP32 outputs (device memory).
  *   ctx    : NULL, or receives the context the backward needs (device
  *            memory for P, the vectors P^t e_s and the partial sums, about
- *            (2L + 7) n + 2m words); release it with srk_linear_ctx_free.
+ *            (2L + 5) n + 2m words); release it with srk_linear_ctx_free.
+ * The first call on a graph also builds and keeps in the handle a transpose
+ * of the graph (out-lists in edge order) and the edges' owners, 3m + n words,
+ * released by srk_graph_free.  Results do not depend on timing: every sum is
+ * taken in a fixed order.
  *            The context refers to g, which must outlive it.
  *   cuda_stream : stream to run on; the call synchronises it (to report
  *            non-positive weights as SRK_EINVAL).

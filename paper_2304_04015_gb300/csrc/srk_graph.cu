@@ -252,6 +252,7 @@ extern "C" int srk_graph_free(srk_graph *g) {
     if (g->own_w) cudaFree(g->own_w);
     if (g->adj) cudaFree(g->adj);
     if (g->act) cudaFree(g->act);
+    free_lin_topo(g);
   }
   delete g;
   return rc;

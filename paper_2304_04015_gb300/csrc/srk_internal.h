@@ -28,6 +28,9 @@ struct srk_graph {
   // Launch shape of the batched target kernel chosen by the autotuner
   // (-1: not tuned yet).
   int batch_cfg = -1;
+  // Topology of the linearised form (edge owners, a transpose, list size
+  // classes), built by the first srk_linear_fwd on the graph.
+  struct srk_lin_topo *lin = nullptr;
   int32_t *own_row_ptr = nullptr;    // owned copies (null when borrowed)
   int32_t *own_col = nullptr;
   float *own_w = nullptr;
@@ -109,6 +112,9 @@ int target_range(const srk_graph *g, const srk_opts *opt, int32_t *b, int32_t *e
 // Exclusive scan of cnt[0..N) into off[0..N] (one block of 1024 threads).
 __global__ void k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off,
                        int32_t N);
+
+// Releases the graph's linear topology, if built (srk_linear.cu).
+void free_lin_topo(srk_graph *g);
 
 // Copies the query counters into `stats` (synchronises `st`).
 int read_stats(const QueryTab &t, const Workspace &w, cudaStream_t st,

@@ -13,48 +13,84 @@
 //     G_e = sum_{t=0}^{L-1} ( c gb_t[a] h_{t+1}[u] + yb_{t+1}[u] y_t[a] )
 // (the gradient w.r.t. the entry P[u][a]), and through the normalisation
 //     dLoss/dw_e = ( G_e - sum_{e' in I(a)} G_e' P_e' ) / W_a.
-// P v (a scatter along in-lists) accumulates in FP64 with atomics, so its
-// result does not depend on the order of the additions beyond FP64 rounding;
-// P^T v (a gather along in-lists: one warp per node, one block per node whose
-// in-list is long) is deterministic.  The vectors are stored node-major,
-// n x (L+1), so the per-edge gradient pass reads each node's L values
-// together.
+//
+// Every product with P or P^T is a gather: P^T v along the in-lists, P v along
+// the out-lists of a transpose of the graph that is built once per graph (a
+// stable radix sort of the edges by source node, so each out-list keeps edge
+// order) and cached in the handle.  Each list is reduced in a fixed order by
+// one thread (up to 4 entries), a group of 8 lanes (up to 32), a warp (up to
+// 512) or 256-thread blocks over chunks of 2048 entries whose partial sums
+// are added in chunk order by the block that finishes the list's last chunk,
+// so no result depends on timing.  The vectors are stored node-major, n x (L+1), so the
+// per-edge gradient pass reads each node's L values together.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "srk_internal.h"
+
+namespace srk {
+
+// List size classes of the segmented reductions.
+constexpr int32_t kTiny = 4;      // up to this many entries: one thread
+constexpr int32_t kShort = 32;    // up to this many: 8-lane groups
+constexpr int32_t kMid = 512;     // up to this many: one warp
+constexpr int32_t kChunk = 2048;  // longer lists: chunks of this many entries,
+constexpr int kChunkBlock = 256;  // one block of this many threads per chunk
+constexpr int kGroup = 8;
+// Radix sort of the transpose: 8-bit digits, tiles of 256 threads x 16 keys.
+constexpr int kSortBlock = 256, kSortItems = 16, kSortTile = kSortBlock * kSortItems;
+
+// Size-class lists of one direction (in-lists or out-lists) of the graph.
+struct Classes {
+  int32_t *small = nullptr;       // nodes whose list has kTiny < len <= kShort
+  int32_t *mid = nullptr;         // nodes whose list has kShort < len <= kMid
+  int32_t *item_node = nullptr;   // chunk items of the longer lists: the node,
+  int32_t *item_beg = nullptr;    //   the entry range [beg, end),
+  int32_t *item_end = nullptr;
+  int32_t *item_long = nullptr;   //   the node's index among the long lists
+  int32_t *long_first = nullptr;  // first item and item count of each long list
+  int32_t *long_count = nullptr;
+  int32_t n_small = 0, n_mid = 0, n_long = 0, n_items = 0;
+};
+
+}  // namespace srk
+
+// Per-graph topology of the linearised form (built on first use, freed with
+// the graph).
+struct srk_lin_topo {
+  int32_t *erow = nullptr;     // m: the node whose in-list holds edge e
+  int32_t *out_ptr = nullptr;  // n + 1: out-list offsets of the transpose
+  int32_t *t_a = nullptr;      // m: out-list entry k is the edge (u -> t_a[k]) ...
+  int32_t *t_e = nullptr;      // m: ... of edge index t_e[k] (ascending per list)
+  srk::Classes in, out;
+  void *block = nullptr;
+};
 
 struct srk_linear_ctx {
   const srk_graph *g = nullptr;
+  const srk_lin_topo *topo = nullptr;
   int device = 0;
   int32_t n = 0, L = 0, s = 0;
   int64_t m = 0;
   double c = 0.0;
-  float *Pe = nullptr;     // m: w_e / W_a
-  float *Wa = nullptr;     // n: in-weight sums
-  int32_t *erow = nullptr; // m: the node whose in-list holds edge e
-  float *y = nullptr;      // n x (L+1), node-major: y[a (L+1) + t] = (P^t e_s)[a]
-  float *h = nullptr;      // n x (L+1), node-major partial sums, h_0 = s_vec
-  double *acc = nullptr;   // n: scatter accumulator (zero between uses)
-  int32_t *longs = nullptr;  // nodes whose in-list is longer than kLongRow
-  int32_t *n_long = nullptr; // their count (device)
-  int *bad = nullptr;      // weight check flag
-  void *block = nullptr;   // the device block all arrays above live in
+  float *Pe = nullptr;      // m: w_e / W_a, in-list order
+  float *PeT = nullptr;     // m: the same values in out-list order
+  float *Wa = nullptr;      // n: in-weight sums
+  float *y = nullptr;       // n x (L+1), node-major: y[a (L+1) + t] = (P^t e_s)[a]
+  float *h = nullptr;       // n x (L+1), node-major partial sums, h_0 = s_vec
+  double *part = nullptr;   // partial sums of the chunk items (either direction)
+  int32_t *done = nullptr;  // finished chunks per long list (zero between uses)
+  int *bad = nullptr;       // weight check flag
+  void *block = nullptr;    // the device block all arrays above live in
 };
 
 namespace srk {
 
-// In-lists longer than this are reduced by a whole block instead of a warp,
-// so the hubs of a power-law graph do not serialise on one warp.
-constexpr int32_t kLongRow = 256;
-constexpr int kLongBlock = 1024;
-// Short in-lists are handled by groups of kGroup lanes (4 lists per warp):
-// in-lists average ~16 entries, so a whole warp per list would idle most
-// lanes and serialise the lists' load latencies.
-constexpr int kGroup = 8;
+// ------------------------------------------------------------ reductions --
 
-// Fixed-order reductions (the result does not depend on timing).
 __device__ __forceinline__ double warp_sum(double v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -69,86 +105,302 @@ __device__ __forceinline__ T group_sum(T v) {  // over aligned groups of kGroup 
   return v;
 }
 template <class T>
-__device__ __forceinline__ T block_sum(T v, T *sh) {  // blockDim.x == kLongBlock
+__device__ __forceinline__ T block_sum(T v, T *sh) {  // blockDim.x == kChunkBlock
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) sh[wid] = v;
   __syncthreads();
   T t = 0;
-  if (wid == 0) {
-    t = (lane < kLongBlock / 32) ? sh[lane] : (T)0;
-    t = warp_sum(t);
-    if (lane == 0) sh[0] = t;
+  for (int i = 0; i < kChunkBlock / 32; ++i) t += sh[i];  // same order in every thread
+  return t;
+}
+
+// Sum of val(k) over k in [b, e) taken by thread tid of nthr: four strided
+// entries per round, all loaded before any is added, in a fixed order.
+template <class T, class V>
+__device__ __forceinline__ T list_partial(const V &val, int64_t b, int64_t e, int tid,
+                                          int nthr) {
+  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int64_t k = b + tid; k < e; k += 4 * (int64_t)nthr) {
+    const int64_t k1 = k + nthr, k2 = k + 2 * nthr, k3 = k + 3 * nthr;
+    const T v0 = val(k);
+    const T v1 = (k1 < e) ? val(k1) : (T)0;
+    const T v2 = (k2 < e) ? val(k2) : (T)0;
+    const T v3 = (k3 < e) ? val(k3) : (T)0;
+    s0 += v0;
+    s1 += v1;
+    s2 += v2;
+    s3 += v3;
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+// Entry values and result writers of the segmented reductions.
+struct GatherVal {  // w[k] in[idx[k]], in a column of stride S
+  const int32_t *idx;
+  const float *w;
+  const float *in;
+  int32_t S;
+  __device__ __forceinline__ float operator()(int64_t k) const {
+    return w[k] * in[(int64_t)idx[k] * S];
+  }
+};
+struct DotVal {  // x[k] w[k]
+  const float *x;
+  const float *w;
+  __device__ __forceinline__ float operator()(int64_t k) const { return x[k] * w[k]; }
+};
+struct WeightVal {  // w[k]
+  const float *w;
+  __device__ __forceinline__ float operator()(int64_t k) const { return w[k]; }
+};
+struct WriteAxpy {  // out[a] = alpha add[a] + beta sum (columns of stride S; add may be null)
+  float *out;
+  const float *add;
+  float alpha, beta;
+  int32_t S;
+  __device__ __forceinline__ void operator()(int32_t a, float sum) const {
+    const int64_t i = (int64_t)a * S;
+    out[i] = (add ? alpha * add[i] : 0.0f) + beta * sum;
+  }
+};
+struct WriteVec {  // out[a] = sum
+  float *out;
+  __device__ __forceinline__ void operator()(int32_t a, float sum) const { out[a] = sum; }
+};
+
+// One segmented reduction in one launch, the size classes side by side:
+// blocks [0, nb_long) reduce the chunk items of the lists longer than kMid,
+// the next nb_mid blocks the lists of kShort < len <= kMid (one warp each),
+// the next nb_small blocks those of kTiny < len <= kShort (8-lane groups, 4
+// lists per warp) and the rest every node whose list has at most kTiny
+// entries (one thread each, empty lists included).  A long list's chunk sums
+// are added in chunk order by the block that finishes its last chunk, which
+// then re-arms the list's counter for the next launch.
+template <class T, class V, class W>
+__global__ void __launch_bounds__(kChunkBlock)
+k_seg(const int32_t *__restrict__ ptr, int32_t n, Classes C, V val, W write,
+      T *__restrict__ part, int32_t *__restrict__ done, int32_t nb_long, int32_t nb_mid,
+      int32_t nb_small) {
+  const int32_t bid = blockIdx.x;
+  if (bid < nb_long) {
+    __shared__ T sh[kChunkBlock / 32];
+    __shared__ int last;
+    for (int32_t q = bid; q < C.n_items; q += nb_long) {
+      const T s = block_sum(
+          list_partial<T>(val, C.item_beg[q], C.item_end[q], threadIdx.x, kChunkBlock), sh);
+      const int32_t l = C.item_long[q];
+      if (threadIdx.x == 0) {
+        part[q] = s;
+        __threadfence();
+        last = atomicAdd(&done[l], 1) == C.long_count[l] - 1;
+      }
+      __syncthreads();
+      if (last && threadIdx.x == 0) {
+        __threadfence();
+        const int32_t f = C.long_first[l], cnt = C.long_count[l];
+        const volatile T *p = part;
+        T t = 0;
+        for (int32_t i = 0; i < cnt; ++i) t += p[f + i];
+        write(C.item_node[q], t);
+        done[l] = 0;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  const int32_t b1 = nb_long + nb_mid, b2 = b1 + nb_small;
+  if (bid < b1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)nb_mid * (kChunkBlock / 32);
+    for (int64_t q = ((int64_t)(bid - nb_long) * kChunkBlock + threadIdx.x) / 32; q < C.n_mid;
+         q += warps) {
+      const int32_t a = C.mid[q];
+      const T sum = warp_sum(list_partial<T>(val, ptr[a], ptr[a + 1], lane, 32));
+      if (lane == 0) write(a, sum);
+    }
+  } else if (bid < b2) {
+    // every lane of a warp runs the same number of iterations, so the group
+    // shuffles see all 32 lanes
+    const int gl = threadIdx.x & (kGroup - 1);
+    const int64_t local = (int64_t)(bid - b1) * kChunkBlock + threadIdx.x;
+    const int64_t groups = ((int64_t)nb_small * kChunkBlock) / kGroup;
+    const int64_t warp_first = local / kGroup - ((threadIdx.x & 31) / kGroup);
+    for (int64_t base = warp_first; base < C.n_small; base += groups) {
+      const int64_t q = base + ((threadIdx.x & 31) / kGroup);
+      int32_t a = -1, b = 0, e = 0;
+      if (q < C.n_small) {
+        a = C.small[q];
+        b = ptr[a];
+        e = ptr[a + 1];
+      }
+      const T sum = group_sum(list_partial<T>(val, b, e, gl, kGroup));
+      if (gl == 0 && a >= 0) write(a, sum);
+    }
+  } else {
+    const int64_t threads = (int64_t)(gridDim.x - b2) * kChunkBlock;
+    for (int64_t a = (int64_t)(bid - b2) * kChunkBlock + threadIdx.x; a < n; a += threads) {
+      const int32_t b = ptr[a], e = ptr[a + 1];
+      if (e - b > kTiny) continue;
+      T v[kTiny];
+#pragma unroll
+      for (int j = 0; j < kTiny; ++j) v[j] = (b + j < e) ? val(b + j) : (T)0;
+      write((int32_t)a, (v[0] + v[1]) + (v[2] + v[3]));
+    }
+  }
+}
+
+// ------------------------------------------------------ topology kernels --
+
+// erow[k] = the node a with row_ptr[a] <= k < row_ptr[a+1] (binary search).
+__global__ void k_erow(const int32_t *__restrict__ row_ptr, int32_t n, int64_t m,
+                       int32_t *__restrict__ erow) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = n - 1;  // the largest a with row_ptr[a] <= k
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo + 1) / 2;
+      if (row_ptr[mid] <= k) lo = mid;
+      else hi = mid - 1;
+    }
+    erow[k] = lo;
+  }
+}
+
+__global__ void k_out_degree(const int32_t *__restrict__ col, int64_t m,
+                             int32_t *__restrict__ odeg) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&odeg[col[k]], 1);
+}
+
+__global__ void k_iota(int32_t *__restrict__ v, int64_t m) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[k] = (int32_t)k;
+}
+
+// Radix sort pass, step 1: digit histogram of each tile, stored digit-major
+// (hist[d * tiles + tile]) so that its exclusive scan gives each
+// (digit, tile) its first output position.
+__global__ void __launch_bounds__(kSortBlock)
+k_sort_hist(const int32_t *__restrict__ keys, int64_t m, int shift, int32_t tiles,
+            int32_t *__restrict__ hist) {
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = base + (int64_t)r * kSortBlock + threadIdx.x;
+    if (i < m) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1);
   }
   __syncthreads();
-  return sh[0];
+  hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Nodes with long in-lists (order of the list does not matter: each node's
-// result is computed independently).
-__global__ void k_lin_classify(const int32_t *__restrict__ row_ptr, int32_t n,
-                               int32_t *__restrict__ longs, int32_t *n_long) {
+// Radix sort pass, step 2: stable scatter.  Round r of a tile covers 256
+// consecutive keys; a key goes to its (digit, tile) offset plus the number of
+// keys of its digit in earlier rounds, earlier warps and lower lanes.
+__global__ void __launch_bounds__(kSortBlock)
+k_sort_scatter(const int32_t *__restrict__ keys, const int32_t *__restrict__ vals, int64_t m,
+               int shift, int32_t tiles, const int32_t *__restrict__ off,
+               int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+  constexpr int kWarps = kSortBlock / 32;
+  __shared__ int32_t base[256];
+  __shared__ int32_t wcnt[kWarps][256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  base[t] = off[(int64_t)t * tiles + blockIdx.x];
+  for (int i = 0; i < kWarps; ++i) wcnt[i][t] = 0;
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = tile0 + (int64_t)r * kSortBlock + t;
+    const bool valid = i < m;
+    int32_t key = 0, val = 0, d = 256;  // 256: no key in this slot
+    if (valid) {
+      key = keys[i];
+      val = vals[i];
+      d = (key >> shift) & 255;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    int32_t run = 0;  // thread t: digit t's counts over the warps, made exclusive
+    for (int k = 0; k < kWarps; ++k) {
+      const int32_t c = wcnt[k][t];
+      wcnt[k][t] = run;
+      run += c;
+    }
+    __syncthreads();
+    if (valid) {
+      const int64_t pos = (int64_t)base[d] + wcnt[w][d] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+    base[t] += run;
+    for (int k = 0; k < kWarps; ++k) wcnt[k][t] = 0;
+    __syncthreads();
+  }
+}
+
+__global__ void k_gather_i32(const int32_t *__restrict__ src, const int32_t *__restrict__ idx,
+                             int64_t m, int32_t *__restrict__ dst) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[idx[k]];
+}
+
+// Size classes of the lists of ptr: cnt[0] mid lists, cnt[1] long lists,
+// cnt[2] chunk items, cnt[3] small lists.  Where a node lands in these lists
+// depends on timing; what is computed for the node does not.
+__global__ void k_classify(const int32_t *__restrict__ ptr, int32_t n, Classes C,
+                           int32_t *__restrict__ cnt) {
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n;
-       a += (int64_t)gridDim.x * blockDim.x)
-    if (row_ptr[a + 1] - row_ptr[a] > kLongRow) longs[atomicAdd(n_long, 1)] = (int32_t)a;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = ptr[a], e = ptr[a + 1], len = e - b;
+    if (len > kTiny && len <= kShort) {
+      C.small[atomicAdd(&cnt[3], 1)] = (int32_t)a;
+    } else if (len > kShort && len <= kMid) {
+      C.mid[atomicAdd(&cnt[0], 1)] = (int32_t)a;
+    } else if (len > kMid) {
+      const int32_t l = atomicAdd(&cnt[1], 1);
+      const int32_t c = (len + kChunk - 1) / kChunk;
+      const int32_t f = atomicAdd(&cnt[2], c);
+      C.long_first[l] = f;
+      C.long_count[l] = c;
+      for (int32_t i = 0; i < c; ++i) {
+        C.item_node[f + i] = (int32_t)a;
+        C.item_beg[f + i] = b + i * kChunk;
+        C.item_end[f + i] = min(e, b + (i + 1) * kChunk);
+        C.item_long[f + i] = l;
+      }
+    }
+  }
 }
 
-// W_a, P_e = w_e / W_a and erow for one node; flags weights that are not
-// positive and finite.  Warp version (short lists) and block version.
-__device__ __forceinline__ double prep_partial(const float *w, int32_t b, int32_t e, int32_t a,
-                                               int32_t *erow, int *bad, int tid, int nthr) {
-  double sum = 0.0;
-  for (int32_t k = b + tid; k < e; k += nthr) {
+// ------------------------------------------------------- prep and vectors --
+
+// P_e = w_e / W_a (IEEE FP32 division); flags weights that are not positive
+// and finite.
+__global__ void k_lin_pe(const float *__restrict__ w, const int32_t *__restrict__ erow,
+                         const float *__restrict__ Wa, int64_t m, float *__restrict__ Pe,
+                         int *bad) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
     const float x = w[k];
     if (!(x > 0.0f) || !isfinite(x)) *bad = 1;
-    sum += (double)x;
-    erow[k] = a;
-  }
-  return sum;
-}
-
-// Group loops: every lane of the warp runs the same number of iterations, so
-// the group shuffles see all 32 lanes; nodes past n and long lists are empty.
-#define SRK_GROUP_LOOP(n)                                                         \
-  const int gl = threadIdx.x & (kGroup - 1);                                      \
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / kGroup;              \
-  const int64_t first = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kGroup; \
-  const int64_t warp_first = first - ((threadIdx.x & 31) / kGroup);               \
-  for (int64_t base = warp_first; base < (n); base += groups)
-
-__global__ void k_lin_prep(const int32_t *__restrict__ row_ptr, const float *__restrict__ w,
-                           int32_t n, float *__restrict__ Pe, float *__restrict__ Wa,
-                           int32_t *__restrict__ erow, int *bad) {
-  SRK_GROUP_LOOP(n) {
-    const int64_t a = base + ((threadIdx.x & 31) / kGroup);
-    int32_t b = 0, e = 0;
-    if (a < n) {
-      b = row_ptr[a];
-      e = row_ptr[a + 1];
-      if (e - b > kLongRow) e = b;
-    }
-    const double sum = group_sum(prep_partial(w, b, e, (int32_t)a, erow, bad, gl, kGroup));
-    for (int32_t k = b + gl; k < e; k += kGroup) Pe[k] = (float)((double)w[k] / sum);
-    if (gl == 0 && e > b) Wa[a] = (float)sum;
+    Pe[k] = x / Wa[erow[k]];
   }
 }
 
-__global__ void __launch_bounds__(kLongBlock)
-k_lin_prep_long(const int32_t *__restrict__ row_ptr, const float *__restrict__ w,
-                const int32_t *__restrict__ longs, const int32_t *n_long,
-                float *__restrict__ Pe, float *__restrict__ Wa,
-                int32_t *__restrict__ erow, int *bad) {
-  __shared__ double sh[kLongBlock / 32];
-  const int32_t nl = *n_long;
-  for (int32_t q = blockIdx.x; q < nl; q += gridDim.x) {
-    const int32_t a = longs[q];
-    const int32_t b = row_ptr[a], e = row_ptr[a + 1];
-    const double sum =
-        block_sum(prep_partial(w, b, e, a, erow, bad, threadIdx.x, kLongBlock), sh);
-    for (int32_t k = b + threadIdx.x; k < e; k += kLongBlock) Pe[k] = (float)((double)w[k] / sum);
-    if (threadIdx.x == 0) Wa[a] = (float)sum;
-  }
+__global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__restrict__ idx,
+                             int64_t m, float *__restrict__ dst) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[idx[k]];
 }
 
 // v[a] = (a == s) for a node-major vector column (stride S).
@@ -158,152 +410,253 @@ __global__ void k_lin_unit(float *__restrict__ v, int32_t S, int32_t n, int32_t 
     v[i * S] = (i == s) ? 1.0f : 0.0f;
 }
 
-// acc[u] += P_e v[a] for every edge e = (u -> a); v is a column of stride S.
-__global__ void k_lin_scatter(const float *__restrict__ v, int32_t S,
-                              const float *__restrict__ Pe, const int32_t *__restrict__ col,
-                              const int32_t *__restrict__ erow, int64_t m,
-                              double *__restrict__ acc) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const float va = v[(int64_t)erow[e] * S];
-    if (va != 0.0f) atomicAdd(&acc[col[e]], (double)(Pe[e] * va));
-  }
+// out[a] = d in[a] (columns of stride S).
+__global__ void k_lin_scale(const float *__restrict__ in, float d, int32_t S, int32_t n,
+                            float *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i * S] = d * in[i * S];
 }
 
-// out[u] = scale * acc[u] (column of stride S); acc[u] = 0.
-__global__ void k_lin_finish(double *__restrict__ acc, float scale, int32_t n, int32_t S,
-                             float *__restrict__ out) {
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x) {
-    out[u * S] = (float)(acc[u] * (double)scale);
-    acc[u] = 0.0;
-  }
-}
-
-// out[a] = alpha add[a] + beta sum_{e in I(a)} P_e in[u_e], all three columns
-// of stride S: one warp per short in-list, one block per long in-list.
-__device__ __forceinline__ float gather_partial(const int32_t *col, const float *Pe,
-                                                const float *in, int32_t S, int32_t b,
-                                                int32_t e, int tid, int nthr) {
-  float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-  int32_t k = b + tid;
-  for (; k + 3 * nthr < e; k += 4 * nthr) {  // four independent loads in flight
-    s0 = fmaf(Pe[k], in[(int64_t)col[k] * S], s0);
-    s1 = fmaf(Pe[k + nthr], in[(int64_t)col[k + nthr] * S], s1);
-    s2 = fmaf(Pe[k + 2 * nthr], in[(int64_t)col[k + 2 * nthr] * S], s2);
-    s3 = fmaf(Pe[k + 3 * nthr], in[(int64_t)col[k + 3 * nthr] * S], s3);
-  }
-  for (; k < e; k += nthr) s0 = fmaf(Pe[k], in[(int64_t)col[k] * S], s0);
-  return (s0 + s1) + (s2 + s3);
-}
-
-__global__ void k_lin_gather(const int32_t *__restrict__ row_ptr,
-                             const int32_t *__restrict__ col,
-                             const float *__restrict__ Pe, const float *__restrict__ in,
-                             const float *__restrict__ add, float alpha, float beta,
-                             int32_t n, int32_t S, float *__restrict__ out) {
-  SRK_GROUP_LOOP(n) {
-    const int64_t a = base + ((threadIdx.x & 31) / kGroup);
-    int32_t b = 0, e = 0;
-    if (a < n) {
-      b = row_ptr[a];
-      e = row_ptr[a + 1];
-      if (e - b > kLongRow) e = b - 1;  // handled by the long-list kernel
-    }
-    const float sum = group_sum(gather_partial(col, Pe, in, S, b, e > b ? e : b, gl, kGroup));
-    if (gl == 0 && a < n && e >= b) out[a * S] = alpha * add[a * S] + beta * sum;
-  }
-}
-
-__global__ void __launch_bounds__(kLongBlock)
-k_lin_gather_long(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                  const float *__restrict__ Pe, const float *__restrict__ in,
-                  const float *__restrict__ add, float alpha, float beta, int32_t S,
-                  const int32_t *__restrict__ longs, const int32_t *n_long,
-                  float *__restrict__ out) {
-  __shared__ float sh[kLongBlock / 32];
-  const int32_t nl = *n_long;
-  for (int32_t q = blockIdx.x; q < nl; q += gridDim.x) {
-    const int32_t a = longs[q];
-    const float sum = block_sum(
-        gather_partial(col, Pe, in, S, row_ptr[a], row_ptr[a + 1], threadIdx.x, kLongBlock), sh);
-    if (threadIdx.x == 0) out[(int64_t)a * S] = alpha * add[(int64_t)a * S] + beta * sum;
-  }
-}
-
-// Edge gradients of node a's in-list: G_e, then the normalisation term.
-// Node-major vectors: the L values of h and yb a source node needs are
-// contiguous, and so are the values of gb and y the node a needs.
-__device__ __forceinline__ float edge_G(const float *y, const float *h, const float *gb,
-                                        const float *yb, int32_t S, int32_t L, float c,
-                                        int64_t a, int64_t u) {
-  const float *ga = gb + a * S, *ya = y + a * S, *hu = h + u * S, *ybu = yb + u * S;
-  float G = 0.0f;
-  for (int t = 0; t < L; ++t) {
-    G = fmaf(c * ga[t], hu[t + 1], G);
-    G = fmaf(ybu[t + 1], ya[t], G);
-  }
-  return G;
-}
-
-__global__ void k_lin_edge_grad(const int32_t *__restrict__ row_ptr,
-                                const int32_t *__restrict__ col,
-                                const float *__restrict__ Pe, const float *__restrict__ Wa,
-                                const float *__restrict__ y, const float *__restrict__ h,
-                                const float *__restrict__ gb, const float *__restrict__ yb,
-                                int32_t L, int32_t n, float c, float *__restrict__ grad) {
+// G_e for every edge e = (u -> a), edge-parallel: consecutive edges mostly
+// share a, whose rows of gb and y are then read once per warp.
+__global__ void k_lin_edge_G(const int32_t *__restrict__ erow, const int32_t *__restrict__ col,
+                             int64_t m, const float *__restrict__ y,
+                             const float *__restrict__ h, const float *__restrict__ gb,
+                             const float *__restrict__ yb, int32_t L, float c,
+                             float *__restrict__ G) {
   const int32_t S = L + 1;
-  SRK_GROUP_LOOP(n) {
-    const int64_t a = base + ((threadIdx.x & 31) / kGroup);
-    int32_t b = 0, e = 0;
-    if (a < n) {
-      b = row_ptr[a];
-      e = row_ptr[a + 1];
-      if (e - b > kLongRow) e = b;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = erow[k], u = col[k];
+    const float *ga = gb + a * S, *ya = y + a * S, *hu = h + u * S, *ybu = yb + u * S;
+    float g = 0.0f;
+    for (int t0 = 0; t0 < L; t0 += 4) {  // four terms' loads in flight
+      float gv[4], yv[4], hv[4], bv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int t = t0 + j;
+        const bool ok = t < L;
+        gv[j] = ok ? ga[t] : 0.0f;
+        yv[j] = ok ? ya[t] : 0.0f;
+        hv[j] = ok ? hu[t + 1] : 0.0f;
+        bv[j] = ok ? ybu[t + 1] : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // t ascending; the padding terms add exact zeros
+        g = fmaf(c * gv[j], hv[j], g);
+        g = fmaf(bv[j], yv[j], g);
+      }
     }
-    float T = 0.0f;
-    for (int32_t k = b + gl; k < e; k += kGroup) {
-      const float G = edge_G(y, h, gb, yb, S, L, c, a, col[k]);
-      grad[k] = G;
-      T = fmaf(G, Pe[k], T);
-    }
-    T = group_sum(T);
-    if (e > b) {
-      const float inv = 1.0f / Wa[a];
-      for (int32_t k = b + gl; k < e; k += kGroup) grad[k] = (grad[k] - T) * inv;
-    }
+    G[k] = g;
   }
 }
 
-__global__ void __launch_bounds__(kLongBlock)
-k_lin_edge_grad_long(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                     const float *__restrict__ Pe, const float *__restrict__ Wa,
-                     const float *__restrict__ y, const float *__restrict__ h,
-                     const float *__restrict__ gb, const float *__restrict__ yb, int32_t L,
-                     float c, const int32_t *__restrict__ longs, const int32_t *n_long,
-                     float *__restrict__ grad) {
-  __shared__ float sh[kLongBlock / 32];
-  const int32_t S = L + 1;
-  const int32_t nl = *n_long;
-  for (int32_t q = blockIdx.x; q < nl; q += gridDim.x) {
-    const int32_t a = longs[q];
-    const int32_t b = row_ptr[a], e = row_ptr[a + 1];
-    float T = 0.0f;
-    for (int32_t k = b + threadIdx.x; k < e; k += kLongBlock) {
-      const float G = edge_G(y, h, gb, yb, S, L, c, a, col[k]);
-      grad[k] = G;
-      T = fmaf(G, Pe[k], T);
-    }
-    T = block_sum(T, sh);
-    const float inv = 1.0f / Wa[a];
-    for (int32_t k = b + threadIdx.x; k < e; k += kLongBlock) grad[k] = (grad[k] - T) * inv;
+// grad_e = (G_e - T_a) / W_a with T_a = sum_{e' in I(a)} G_e' P_e'.
+__global__ void k_lin_edge_fin(const int32_t *__restrict__ erow, int64_t m,
+                               const float *__restrict__ T, const float *__restrict__ Wa,
+                               float *__restrict__ grad) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = erow[k];
+    grad[k] = (grad[k] - T[a]) * (1.0f / Wa[a]);
   }
 }
 
-static int grid_of(int64_t work, int per_block, int dev) {
+// ------------------------------------------------------------- host side --
+
+static int grid_of(int64_t work, int per_block, int dev, int per_sm = 8) {
   const int64_t want = (work + per_block - 1) / per_block;
-  const int64_t cap = (int64_t)sm_count(dev) * 16;
+  const int64_t cap = (int64_t)sm_count(dev) * per_sm;
   return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+// Segmented reduction over the lists of ptr (size classes C) in one launch of
+// up to 8 x SMs blocks, split between the classes by their estimated rounds
+// of work per block: a chunk item about three rounds of a block, a mid list
+// about two rounds of a warp (8 per block), a small list one round of an
+// 8-lane group (32 per block), any node one round of a thread (256 per block).
+template <class T, class V, class W>
+static void segmented(const int32_t *ptr, int32_t n, const Classes &C, V val, W write,
+                      double *part, int32_t *done, int dev, cudaStream_t st) {
+  const int64_t blocks = (int64_t)sm_count(dev) * 8;
+  const double w_long = 3.0 * C.n_items, w_mid = 2.0 * C.n_mid / 8.0,
+               w_small = C.n_small / 32.0, w_tiny = n / 256.0;
+  const double w_all = w_long + w_mid + w_small + w_tiny;
+  auto share = [&](double w, int64_t cap) -> int64_t {
+    if (cap <= 0) return 0;
+    int64_t b = (int64_t)(blocks * w / w_all);
+    if (b < 1) b = 1;
+    return b > cap ? cap : b;
+  };
+  const int64_t nb_long = share(w_long, C.n_items);
+  const int64_t nb_mid = share(w_mid, ((int64_t)C.n_mid + 7) / 8);
+  const int64_t nb_small = share(w_small, ((int64_t)C.n_small + 31) / 32);
+  const int64_t nb_tiny = share(w_tiny, ((int64_t)n + 255) / 256);
+  k_seg<T><<<(int)(nb_long + nb_mid + nb_small + nb_tiny), kChunkBlock, 0, st>>>(
+      ptr, n, C, val, write, reinterpret_cast<T *>(part), done, (int32_t)nb_long,
+      (int32_t)nb_mid, (int32_t)nb_small);
+}
+
+// out = alpha add + beta P^T in (columns of stride S; gather along in-lists).
+static void gather_t(const srk_linear_ctx *x, const float *in, const float *add, float alpha,
+                     float beta, float *out, cudaStream_t st) {
+  const int32_t S = x->L + 1;
+  segmented<float>(x->g->row_ptr, x->n, x->topo->in, GatherVal{x->g->col, x->Pe, in, S},
+                   WriteAxpy{out, add, alpha, beta, S}, x->part, x->done, x->device, st);
+}
+
+// out = scale P in (columns of stride S; gather along the transpose's out-lists).
+static void gather_p(const srk_linear_ctx *x, const float *in, float scale, float *out,
+                     cudaStream_t st) {
+  const int32_t S = x->L + 1;
+  segmented<float>(x->topo->out_ptr, x->n, x->topo->out,
+                   GatherVal{x->topo->t_a, x->PeT, in, S}, WriteAxpy{out, nullptr, 0.0f, scale, S},
+                   x->part, x->done, x->device, st);
+}
+
+// Capacities of the class arrays of one direction.
+static size_t long_lists_max(int64_t m) { return (size_t)(m / (kMid + 1)) + 1; }
+static size_t items_max(int64_t m) { return (size_t)(m / kChunk) + long_lists_max(m) + 1; }
+static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Carves the class arrays of one direction from p (sizes only when p is
+// null); returns the bytes used.
+static size_t class_layout(Classes *C, char *p, int32_t n, int64_t m) {
+  const size_t sizes[8] = {(size_t)n,    (size_t)n,         items_max(m),     items_max(m),
+                           items_max(m), items_max(m),      long_lists_max(m), long_lists_max(m)};
+  int32_t **dst[8] = {&C->small,     &C->mid,        &C->item_node,  &C->item_beg,
+                      &C->item_end,  &C->item_long,  &C->long_first, &C->long_count};
+  size_t off = 0;
+  for (int i = 0; i < 8; ++i) {
+    if (p) *dst[i] = reinterpret_cast<int32_t *>(p + off);
+    off += up256(sizeof(int32_t) * sizes[i]);
+  }
+  return off;
+}
+
+static std::mutex topo_mu;
+
+// Builds g's linear topology on stream st and waits for it.
+static int build_topo(const srk_graph *g, cudaStream_t st, srk_lin_topo **out) {
+  const int dev = g->device;
+  const int32_t n = g->n;
+  const int64_t m = g->m;
+  const size_t mm = (size_t)(m > 0 ? m : 1);
+  const size_t words_m = up256(sizeof(int32_t) * mm);
+  Classes sizing;
+  const size_t cls = class_layout(&sizing, nullptr, n, m);
+  const size_t keep = 3 * words_m + up256(sizeof(int32_t) * ((size_t)n + 1)) + 2 * cls;
+  srk_lin_topo *T = new srk_lin_topo;
+  cudaError_t e = cudaMalloc(&T->block, keep);
+  if (e != cudaSuccess) {
+    delete T;
+    return cuda_fail(e, "linear topology: allocation");
+  }
+  char *p = (char *)T->block;
+  T->erow = (int32_t *)p;
+  T->t_a = (int32_t *)(p + words_m);
+  T->t_e = (int32_t *)(p + 2 * words_m);
+  T->out_ptr = (int32_t *)(p + 3 * words_m);
+  p += 3 * words_m + up256(sizeof(int32_t) * ((size_t)n + 1));
+  p += class_layout(&T->in, p, n, m);
+  class_layout(&T->out, p, n, m);
+
+  // scratch: out-degrees, two key/value buffers, histogram and its scan, counters
+  const int32_t tiles = (int32_t)((m + kSortTile - 1) / kSortTile);
+  const size_t H = (size_t)256 * (size_t)(tiles > 0 ? tiles : 1);
+  const size_t scratch = up256(sizeof(int32_t) * (size_t)n) + 4 * words_m +
+                         up256(sizeof(int32_t) * H) + up256(sizeof(int32_t) * (H + 1)) +
+                         up256(sizeof(int32_t) * 8);
+  cudaMemPool_t mp = pool(dev);
+  void *sb = nullptr;
+  e = mp ? cudaMallocFromPoolAsync(&sb, scratch, mp, st) : cudaErrorMemoryAllocation;
+  if (e != cudaSuccess) {
+    cudaFree(T->block);
+    delete T;
+    return cuda_fail(e, "linear topology: scratch");
+  }
+  char *q = (char *)sb;
+  int32_t *odeg = (int32_t *)q;
+  q += up256(sizeof(int32_t) * (size_t)n);
+  int32_t *kA = (int32_t *)q, *vA = (int32_t *)(q + words_m);
+  int32_t *kB = (int32_t *)(q + 2 * words_m), *vB = (int32_t *)(q + 3 * words_m);
+  q += 4 * words_m;
+  int32_t *hist = (int32_t *)q;
+  q += up256(sizeof(int32_t) * H);
+  int32_t *hoff = (int32_t *)q;
+  q += up256(sizeof(int32_t) * (H + 1));
+  int32_t *cnt = (int32_t *)q;
+
+  const int gm = grid_of(m, 256, dev), gn = grid_of(n, 256, dev);
+  cudaMemsetAsync(odeg, 0, sizeof(int32_t) * (size_t)n, st);
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 8, st);
+  if (m > 0) {
+    k_erow<<<gm, 256, 0, st>>>(g->row_ptr, n, m, T->erow);
+    k_out_degree<<<gm, 256, 0, st>>>(g->col, m, odeg);
+  }
+  k_scan<<<1, 1024, 0, st>>>(odeg, T->out_ptr, n);
+  if (m > 0) {
+    // stable LSD radix sort of the edge indices by their source node col[e]
+    cudaMemcpyAsync(kA, g->col, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    k_iota<<<gm, 256, 0, st>>>(vA, m);
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) ++bits;  // keys < n <= 2^bits
+    for (int shift = 0; shift < bits; shift += 8) {
+      k_sort_hist<<<tiles, kSortBlock, 0, st>>>(kA, m, shift, tiles, hist);
+      k_scan<<<1, 1024, 0, st>>>(hist, hoff, (int32_t)H);
+      k_sort_scatter<<<tiles, kSortBlock, 0, st>>>(kA, vA, m, shift, tiles, hoff, kB, vB);
+      int32_t *tk = kA, *tv = vA;
+      kA = kB;
+      vA = vB;
+      kB = tk;
+      vB = tv;
+    }
+    cudaMemcpyAsync(T->t_e, vA, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    k_gather_i32<<<gm, 256, 0, st>>>(T->erow, T->t_e, m, T->t_a);
+  }
+  k_classify<<<gn, 256, 0, st>>>(g->row_ptr, n, T->in, cnt);
+  k_classify<<<gn, 256, 0, st>>>(T->out_ptr, n, T->out, cnt + 4);
+  int32_t hc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(sb, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    cudaFree(T->block);
+    delete T;
+    return cuda_fail(e, "linear topology: build");
+  }
+  T->in.n_mid = hc[0];
+  T->in.n_long = hc[1];
+  T->in.n_items = hc[2];
+  T->in.n_small = hc[3];
+  T->out.n_mid = hc[4];
+  T->out.n_long = hc[5];
+  T->out.n_items = hc[6];
+  T->out.n_small = hc[7];
+  *out = T;
+  return SRK_OK;
+}
+
+static int get_topo(const srk_graph *g, cudaStream_t st, const srk_lin_topo **out) {
+  std::lock_guard<std::mutex> lock(topo_mu);
+  if (!g->lin) {
+    srk_lin_topo *T = nullptr;
+    const int rc = build_topo(g, st, &T);
+    if (rc != SRK_OK) return rc;
+    const_cast<srk_graph *>(g)->lin = T;
+  }
+  *out = g->lin;
+  return SRK_OK;
+}
+
+void free_lin_topo(srk_graph *g) {
+  if (!g || !g->lin) return;
+  if (g->lin->block) cudaFree(g->lin->block);
+  delete g->lin;
+  g->lin = nullptr;
 }
 
 // The context's device memory is one block from the library's stream-ordered
@@ -313,28 +666,6 @@ static void free_ctx(srk_linear_ctx *x, cudaStream_t st = nullptr) {
   DeviceGuard guard(x->device);
   if (x->block) cudaFreeAsync(x->block, st);
   delete x;
-}
-
-// out = alpha add + beta P^T in (columns of stride S): short and long lists.
-static void gather(const srk_linear_ctx *x, const float *in, const float *add, float alpha,
-                   float beta, float *out, cudaStream_t st) {
-  const srk_graph *g = x->g;
-  const int32_t S = x->L + 1;
-  const int gw = grid_of((int64_t)x->n * kGroup, 256, x->device);
-  k_lin_gather<<<gw, 256, 0, st>>>(g->row_ptr, g->col, x->Pe, in, add, alpha, beta, x->n, S,
-                                   out);
-  k_lin_gather_long<<<sm_count(x->device) * 2, kLongBlock, 0, st>>>(
-      g->row_ptr, g->col, x->Pe, in, add, alpha, beta, S, x->longs, x->n_long, out);
-}
-
-// out = scale P in (columns of stride S), through the FP64 accumulator.
-static void scatter(const srk_linear_ctx *x, const float *in, float scale, float *out,
-                    cudaStream_t st) {
-  const srk_graph *g = x->g;
-  const int32_t S = x->L + 1;
-  const int gm = grid_of(x->m, 256, x->device), gn = grid_of(x->n, 256, x->device);
-  k_lin_scatter<<<gm, 256, 0, st>>>(in, S, x->Pe, g->col, x->erow, x->m, x->acc);
-  k_lin_finish<<<gn, 256, 0, st>>>(x->acc, scale, x->n, S, out);
 }
 
 }  // namespace srk
@@ -368,8 +699,12 @@ extern "C" int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s
     return fail(SRK_EINVAL, "srk_linear_fwd takes device pointers for edge_w and s_out");
   const int dev = g->device;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  const srk_lin_topo *topo = nullptr;
+  const int rc = get_topo(g, st, &topo);
+  if (rc != SRK_OK) return rc;
   srk_linear_ctx *x = new srk_linear_ctx;
   x->g = g;
+  x->topo = topo;
   x->device = dev;
   x->n = g->n;
   x->m = g->m;
@@ -379,12 +714,12 @@ extern "C" int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s
   const size_t n = (size_t)g->n, m = (size_t)(g->m > 0 ? g->m : 1);
   const int32_t S = L + 1;
   const size_t vec = (size_t)S * n;
-  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sizes[9] = {sizeof(float) * m, sizeof(float) * n, sizeof(int32_t) * m,
-                           sizeof(float) * vec, sizeof(float) * vec, sizeof(double) * n,
-                           sizeof(int32_t) * n, sizeof(int32_t), sizeof(int)};
+  const size_t cap = items_max(g->m) + long_lists_max(g->m);
+  const size_t sizes[8] = {sizeof(float) * m,   sizeof(float) * m,     sizeof(float) * n,
+                           sizeof(float) * vec, sizeof(float) * vec,   sizeof(double) * cap,
+                           sizeof(int32_t) * cap, sizeof(int)};
   size_t total = 0;
-  for (size_t b : sizes) total += up(b);
+  for (size_t b : sizes) total += up256(b);
   cudaMemPool_t mp = pool(dev);
   if (!mp) {
     delete x;
@@ -398,30 +733,30 @@ extern "C" int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s
   }
   {
     char *p = (char *)x->block;
-    void **dst[9] = {(void **)&x->Pe, (void **)&x->Wa, (void **)&x->erow, (void **)&x->y,
-                     (void **)&x->h, (void **)&x->acc, (void **)&x->longs,
-                     (void **)&x->n_long, (void **)&x->bad};
-    for (int i = 0; i < 9; ++i) {
+    void **dst[8] = {(void **)&x->Pe,   (void **)&x->PeT,  (void **)&x->Wa,
+                     (void **)&x->y,    (void **)&x->h,    (void **)&x->part,
+                     (void **)&x->done, (void **)&x->bad};
+    for (int i = 0; i < 8; ++i) {
       *dst[i] = p;
-      p += up(sizes[i]);
+      p += up256(sizes[i]);
     }
   }
-  const int gn = grid_of((int64_t)n, 256, dev), gw = grid_of((int64_t)n * kGroup, 256, dev);
+  const int gn = grid_of((int64_t)n, 256, dev), gm = grid_of(g->m, 256, dev);
   const float fc = (float)c, d = (float)(1.0 - c);
-  e = cudaSuccess;
-  cudaMemsetAsync(x->acc, 0, sizeof(double) * n, st);
+  cudaMemsetAsync(x->done, 0, sizeof(int32_t) * cap, st);
   cudaMemsetAsync(x->bad, 0, sizeof(int), st);
-  cudaMemsetAsync(x->n_long, 0, sizeof(int32_t), st);
-  k_lin_classify<<<gn, 256, 0, st>>>(g->row_ptr, g->n, x->longs, x->n_long);
-  k_lin_prep<<<gw, 256, 0, st>>>(g->row_ptr, edge_w, g->n, x->Pe, x->Wa, x->erow, x->bad);
-  k_lin_prep_long<<<sm_count(dev) * 2, kLongBlock, 0, st>>>(g->row_ptr, edge_w, x->longs,
-                                                            x->n_long, x->Pe, x->Wa, x->erow,
-                                                            x->bad);
+  // W_a (FP32 sums in a fixed order), then P in in-list and in out-list order
+  segmented<float>(g->row_ptr, g->n, topo->in, WeightVal{edge_w}, WriteVec{x->Wa}, x->part,
+                   x->done, dev, st);
+  if (g->m > 0) {
+    k_lin_pe<<<gm, 256, 0, st>>>(edge_w, topo->erow, x->Wa, g->m, x->Pe, x->bad);
+    k_gather_f32<<<gm, 256, 0, st>>>(x->Pe, topo->t_e, g->m, x->PeT);
+  }
   k_lin_unit<<<gn, 256, 0, st>>>(x->y, S, g->n, s);
-  for (int t = 1; t <= L; ++t) scatter(x, x->y + (t - 1), 1.0f, x->y + t, st);  // y_t = P y_{t-1}
-  // h_L = D y_L (a gather with beta = 0), then h_t = D y_t + c P^T h_{t+1}
-  gather(x, x->y + L, x->y + L, d, 0.0f, x->h + L, st);
-  for (int t = L - 1; t >= 0; --t) gather(x, x->h + (t + 1), x->y + t, d, fc, x->h + t, st);
+  for (int t = 1; t <= L; ++t) gather_p(x, x->y + (t - 1), 1.0f, x->y + t, st);  // y_t = P y_{t-1}
+  // h_L = D y_L, then h_t = D y_t + c P^T h_{t+1}
+  k_lin_scale<<<gn, 256, 0, st>>>(x->y + L, d, S, g->n, x->h + L);
+  for (int t = L - 1; t >= 0; --t) gather_t(x, x->h + (t + 1), x->y + t, d, fc, x->h + t, st);
   // s_out = column 0 of h (stride S)
   e = cudaMemcpy2DAsync(s_out, sizeof(float), x->h, sizeof(float) * S, sizeof(float), n,
                         cudaMemcpyDeviceToDevice, st);
@@ -451,6 +786,7 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
   if (!is_device_ptr(grad_s) || (x->m > 0 && !is_device_ptr(grad_w)))
     return fail(SRK_EINVAL, "srk_linear_bwd takes device pointers");
   const srk_graph *g = x->g;
+  const srk_lin_topo *topo = x->topo;
   const int dev = x->device;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const size_t n = (size_t)x->n;
@@ -460,27 +796,28 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
   cudaMemPool_t mp = pool(dev);
   if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
   float *gb = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync((void **)&gb, sizeof(float) * 2 * vec, mp, st);
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&gb, sizeof(float) * (2 * vec + n), mp, st);
   if (e != cudaSuccess) return cuda_fail(e, "srk_linear_bwd: allocation");
-  float *yb = gb + vec;
-  const int gw = grid_of((int64_t)n * kGroup, 256, dev);
+  float *yb = gb + vec, *T = gb + 2 * vec;
+  const int gn = grid_of((int64_t)n, 256, dev), gm = grid_of(x->m, 256, dev);
   const float fc = (float)x->c, d = (float)(1.0 - x->c);
   // gb column 0 = g (stride S)
   cudaMemcpy2DAsync(gb, sizeof(float) * S, grad_s, sizeof(float), sizeof(float), n,
                     cudaMemcpyDeviceToDevice, st);
-  for (int t = 1; t <= L; ++t) scatter(x, gb + (t - 1), fc, gb + t, st);  // gb_t = c P gb_{t-1}
+  for (int t = 1; t <= L; ++t) gather_p(x, gb + (t - 1), fc, gb + t, st);  // gb_t = c P gb_{t-1}
   if (L >= 1) {
     // yb_L = D gb_L, yb_t = D gb_t + P^T yb_{t+1} for t = L-1 .. 1
-    gather(x, gb + L, gb + L, d, 0.0f, yb + L, st);
-    for (int t = L - 1; t >= 1; --t) gather(x, yb + (t + 1), gb + t, d, 1.0f, yb + t, st);
+    k_lin_scale<<<gn, 256, 0, st>>>(gb + L, d, S, x->n, yb + L);
+    for (int t = L - 1; t >= 1; --t) gather_t(x, yb + (t + 1), gb + t, d, 1.0f, yb + t, st);
   }
   if (x->m > 0) {
     if (L >= 1) {
-      k_lin_edge_grad<<<gw, 256, 0, st>>>(g->row_ptr, g->col, x->Pe, x->Wa, x->y, x->h, gb, yb,
-                                          L, x->n, fc, grad_w);
-      k_lin_edge_grad_long<<<sm_count(dev) * 2, kLongBlock, 0, st>>>(
-          g->row_ptr, g->col, x->Pe, x->Wa, x->y, x->h, gb, yb, L, fc, x->longs, x->n_long,
-          grad_w);
+      // G_e into grad_w, T_a = sum G_e P_e per in-list, then the normalisation
+      k_lin_edge_G<<<gm, 256, 0, st>>>(topo->erow, g->col, x->m, x->y, x->h, gb, yb, L, fc,
+                                       grad_w);
+      segmented<float>(g->row_ptr, x->n, topo->in, DotVal{grad_w, x->Pe}, WriteVec{T}, x->part,
+                       x->done, dev, st);
+      k_lin_edge_fin<<<gm, 256, 0, st>>>(topo->erow, x->m, T, x->Wa, grad_w);
     } else {
       cudaMemsetAsync(grad_w, 0, sizeof(float) * (size_t)x->m, st);  // s_vec = D e_s
     }

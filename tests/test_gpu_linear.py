@@ -122,3 +122,40 @@ def test_linear_invalid_weights_and_source(srk):
         ctx.free()
     finally:
         graph.close()
+
+
+def hub_graph(n=12000, seed=5):
+    """ER in-lists plus a node whose in-list holds every other node (a list of
+    six 2048-entry chunks), a node with 300 in-neighbours (a warp-sized list)
+    and a node that is an in-neighbour of 5000 others (a long out-list of the
+    transpose); in-lists sorted, no duplicates."""
+    from srk_inputs import csr_from_edges, er_in_csr
+    rp, col = er_in_csr(n, 4.0, seed=seed)
+    dst = np.repeat(np.arange(n), np.diff(rp))
+    src = col.astype(np.int64)
+    hub_in = np.arange(1, n)
+    fan = np.arange(2, 5002)
+    mid = np.arange(100, 400)
+    dst = np.concatenate([dst, np.zeros(hub_in.size, np.int64), fan, np.full(mid.size, 2)])
+    src = np.concatenate([src, hub_in, np.ones(fan.size, np.int64), mid])
+    return csr_from_edges(n, src, dst)
+
+
+def test_hub_lists_every_size_class_and_bitwise_determinism(srk):
+    from oracle import linear
+    from srk_inputs import lognormal_weights
+    rp, col = hub_graph()
+    n = rp.size - 1
+    deg = np.diff(rp)
+    outdeg = np.bincount(col, minlength=n)
+    assert deg.max() > 6 * 2048 - 2048 and outdeg.max() >= 5000
+    assert np.any((deg > 32) & (deg <= 512)) and np.any(deg <= 32)
+    w = lognormal_weights(col.size, seed=9)
+    g = np.random.default_rng(8).normal(size=n)
+    for s in (0, 1, 7):
+        a = run_gpu(srk, rp, col, w, s, 8, g)
+        b = run_gpu(srk, rp, col, w, s, 8, g)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        ref_g, ref_s = linear.grad(rp, col, w.astype(np.float64), n, s, C, 8, g)
+        check_forward(a[0], ref_s)
+        check_grad(a[1], ref_g)

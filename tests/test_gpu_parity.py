@@ -401,3 +401,20 @@ def test_literal_shuffle_rmat_sampled_targets_and_ranges(srk):
                                  literal_shuffle=True)
     finally:
         g.close()
+
+
+def test_walk_count_near_the_limit_sampled_targets(srk):
+    # N_tot just below SRK_MAX_WALKS = 2^24: the Fisher-Yates resolution, the
+    # pair list and the hit table at their largest, checked on sampled targets
+    from oracle.params import sample_table
+    rp, col = er_graph(1000, 5.0, 1)
+    L = 16
+    z = float(srk.SRK_MAX_WALKS)
+    for _ in range(3):   # N_tot is z times the kept mass plus the round-ups
+        z += srk.SRK_MAX_WALKS - 100 - sample_table(1000, C, 0.1, z_override=z, L_override=L).N_tot
+    gpu = gpu_query(srk, rp, col, 3, 0.1, 21, z_override=z, L_override=L,
+                    device_outputs=False)
+    assert srk.SRK_MAX_WALKS - 400 < gpu[4].n_walks <= srk.SRK_MAX_WALKS
+    targets = np.array([0, 1, 2, 500, 998, 999], dtype=np.int64)
+    ref = oracle_query(rp, col, 3, 0.1, 21, targets=targets, z_override=z, L_override=L)
+    assert_parity(gpu, ref, targets)
