@@ -19,9 +19,9 @@
 // stable radix sort of the edges by source node, so each out-list keeps edge
 // order) and cached in the handle.  Each list is reduced in a fixed order by
 // one thread (up to 4 entries), a group of 8 lanes (up to 32), a warp (up to
-// 512) or 256-thread blocks over chunks of 2048 entries whose partial sums
-// are added in chunk order by the block that finishes the list's last chunk,
-// so no result depends on timing.  The vectors are stored node-major, n x (L+1), so the
+// 512), or warps over chunks of 512 entries whose partial sums are added in
+// chunk order by the warp that finishes the list's last chunk, so no result
+// depends on timing.  The vectors are stored node-major, n x (L+1), so the
 // per-edge gradient pass reads each node's L values together.
 #include <math.h>
 #include <stdint.h>
@@ -37,16 +37,16 @@ namespace srk {
 constexpr int32_t kTiny = 4;      // up to this many entries: one thread
 constexpr int32_t kShort = 32;    // up to this many: 8-lane groups
 constexpr int32_t kMid = 512;     // up to this many: one warp
-constexpr int32_t kChunk = 2048;  // longer lists: chunks of this many entries,
-constexpr int kChunkBlock = 256;  // one block of this many threads per chunk
+constexpr int32_t kChunk = 512;   // longer lists: chunks of this many entries, one warp each
 constexpr int kGroup = 8;
+constexpr int kSegBlock = 256;    // threads per block of the reduction kernel
 // Radix sort of the transpose: 8-bit digits, tiles of 256 threads x 16 keys.
 constexpr int kSortBlock = 256, kSortItems = 16, kSortTile = kSortBlock * kSortItems;
 
 // Size-class lists of one direction (in-lists or out-lists) of the graph.
 struct Classes {
-  int32_t *small = nullptr;       // nodes whose list has kTiny < len <= kShort
-  int32_t *mid = nullptr;         // nodes whose list has kShort < len <= kMid
+  int4 *small = nullptr;          // {node, beg, end, 0} of the lists with kTiny < len <= kShort
+  int4 *mid = nullptr;            // {node, beg, end, 0} of the lists with kShort < len <= kMid
   int32_t *item_node = nullptr;   // chunk items of the longer lists: the node,
   int32_t *item_beg = nullptr;    //   the entry range [beg, end),
   int32_t *item_end = nullptr;
@@ -104,18 +104,6 @@ __device__ __forceinline__ T group_sum(T v) {  // over aligned groups of kGroup 
   for (int off = kGroup / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
-template <class T>
-__device__ __forceinline__ T block_sum(T v, T *sh) {  // blockDim.x == kChunkBlock
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  T t = 0;
-  for (int i = 0; i < kChunkBlock / 32; ++i) t += sh[i];  // same order in every thread
-  return t;
-}
-
 // Sum of val(k) over k in [b, e) taken by thread tid of nthr: four strided
 // entries per round, all loaded before any is added, in a fixed order.
 template <class T, class V>
@@ -170,83 +158,85 @@ struct WriteVec {  // out[a] = sum
   __device__ __forceinline__ void operator()(int32_t a, float sum) const { out[a] = sum; }
 };
 
-// One segmented reduction in one launch, the size classes side by side:
-// blocks [0, nb_long) reduce the chunk items of the lists longer than kMid,
-// the next nb_mid blocks the lists of kShort < len <= kMid (one warp each),
-// the next nb_small blocks those of kTiny < len <= kShort (8-lane groups, 4
-// lists per warp) and the rest every node whose list has at most kTiny
-// entries (one thread each, empty lists included).  A long list's chunk sums
-// are added in chunk order by the block that finishes its last chunk, which
-// then re-arms the list's counter for the next launch.
+// One segmented reduction over the work units, in this order: the chunks of
+// the lists longer than kMid (one warp each), the lists of kShort < len <=
+// kMid (one warp each), groups of 8 lists of kTiny < len <= kShort (two per
+// 8 lanes) and runs of 64 consecutive nodes, of which each lane reduces the
+// lists of two nodes that have at most kTiny entries (empty lists included).  Warp w
+// of the grid takes units w, w + W, w + 2W, ... (W warps), so every warp gets
+// a like mix of the classes.  A long list's chunk sums are added in chunk
+// order by the warp that finishes its last chunk, which then re-arms the
+// list's counter for the next launch.
 template <class T, class V, class W>
-__global__ void __launch_bounds__(kChunkBlock)
+__global__ void __launch_bounds__(kSegBlock)
 k_seg(const int32_t *__restrict__ ptr, int32_t n, Classes C, V val, W write,
-      T *__restrict__ part, int32_t *__restrict__ done, int32_t nb_long, int32_t nb_mid,
-      int32_t nb_small) {
-  const int32_t bid = blockIdx.x;
-  if (bid < nb_long) {
-    __shared__ T sh[kChunkBlock / 32];
-    __shared__ int last;
-    for (int32_t q = bid; q < C.n_items; q += nb_long) {
-      const T s = block_sum(
-          list_partial<T>(val, C.item_beg[q], C.item_end[q], threadIdx.x, kChunkBlock), sh);
-      const int32_t l = C.item_long[q];
-      if (threadIdx.x == 0) {
-        part[q] = s;
+      T *__restrict__ part, int32_t *__restrict__ done) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e1 = C.n_items, e2 = e1 + C.n_mid, e3 = e2 + ((int64_t)C.n_small + 7) / 8,
+                e4 = e3 + ((int64_t)n + 63) / 64;
+  const int64_t W_all = ((int64_t)gridDim.x * blockDim.x) / 32;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < e4; u += W_all) {
+    if (u < e1) {
+      const T s = warp_sum(list_partial<T>(val, C.item_beg[u], C.item_end[u], lane, 32));
+      if (lane == 0) {
+        const int32_t l = C.item_long[u];
+        part[u] = s;
         __threadfence();
-        last = atomicAdd(&done[l], 1) == C.long_count[l] - 1;
+        if (atomicAdd(&done[l], 1) == C.long_count[l] - 1) {
+          __threadfence();
+          const int32_t f = C.long_first[l], cnt = C.long_count[l];
+          const volatile T *p = part;
+          T t = 0;
+          for (int32_t i = 0; i < cnt; ++i) t += p[f + i];
+          write(C.item_node[u], t);
+          done[l] = 0;
+        }
       }
-      __syncthreads();
-      if (last && threadIdx.x == 0) {
-        __threadfence();
-        const int32_t f = C.long_first[l], cnt = C.long_count[l];
-        const volatile T *p = part;
-        T t = 0;
-        for (int32_t i = 0; i < cnt; ++i) t += p[f + i];
-        write(C.item_node[q], t);
-        done[l] = 0;
-      }
-      __syncthreads();
-    }
-    return;
-  }
-  const int32_t b1 = nb_long + nb_mid, b2 = b1 + nb_small;
-  if (bid < b1) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)nb_mid * (kChunkBlock / 32);
-    for (int64_t q = ((int64_t)(bid - nb_long) * kChunkBlock + threadIdx.x) / 32; q < C.n_mid;
-         q += warps) {
-      const int32_t a = C.mid[q];
-      const T sum = warp_sum(list_partial<T>(val, ptr[a], ptr[a + 1], lane, 32));
-      if (lane == 0) write(a, sum);
-    }
-  } else if (bid < b2) {
-    // every lane of a warp runs the same number of iterations, so the group
-    // shuffles see all 32 lanes
-    const int gl = threadIdx.x & (kGroup - 1);
-    const int64_t local = (int64_t)(bid - b1) * kChunkBlock + threadIdx.x;
-    const int64_t groups = ((int64_t)nb_small * kChunkBlock) / kGroup;
-    const int64_t warp_first = local / kGroup - ((threadIdx.x & 31) / kGroup);
-    for (int64_t base = warp_first; base < C.n_small; base += groups) {
-      const int64_t q = base + ((threadIdx.x & 31) / kGroup);
-      int32_t a = -1, b = 0, e = 0;
-      if (q < C.n_small) {
-        a = C.small[q];
-        b = ptr[a];
-        e = ptr[a + 1];
-      }
-      const T sum = group_sum(list_partial<T>(val, b, e, gl, kGroup));
-      if (gl == 0 && a >= 0) write(a, sum);
-    }
-  } else {
-    const int64_t threads = (int64_t)(gridDim.x - b2) * kChunkBlock;
-    for (int64_t a = (int64_t)(bid - b2) * kChunkBlock + threadIdx.x; a < n; a += threads) {
-      const int32_t b = ptr[a], e = ptr[a + 1];
-      if (e - b > kTiny) continue;
-      T v[kTiny];
+    } else if (u < e2) {
+      const int4 r = C.mid[u - e1];
+      const T sum = warp_sum(list_partial<T>(val, r.y, r.z, lane, 32));
+      if (lane == 0) write(r.x, sum);
+    } else if (u < e3) {
+      // two lists per 8-lane group, each at most 4 entries per lane, loaded
+      // together
+      const int gl = lane & (kGroup - 1);
+      const int64_t q0 = (u - e2) * 8 + lane / kGroup, q1 = q0 + 4;
+      const int4 r0 = q0 < C.n_small ? C.small[q0] : make_int4(-1, 0, 0, 0);
+      const int4 r1 = q1 < C.n_small ? C.small[q1] : make_int4(-1, 0, 0, 0);
+      T v0[4], v1[4];
 #pragma unroll
-      for (int j = 0; j < kTiny; ++j) v[j] = (b + j < e) ? val(b + j) : (T)0;
-      write((int32_t)a, (v[0] + v[1]) + (v[2] + v[3]));
+      for (int j = 0; j < 4; ++j) {
+        const int32_t k0 = r0.y + gl + j * kGroup, k1 = r1.y + gl + j * kGroup;
+        v0[j] = k0 < r0.z ? val(k0) : (T)0;
+        v1[j] = k1 < r1.z ? val(k1) : (T)0;
+      }
+      const T s0 = group_sum((v0[0] + v0[1]) + (v0[2] + v0[3]));
+      const T s1 = group_sum((v1[0] + v1[1]) + (v1[2] + v1[3]));
+      if (gl == 0 && r0.x >= 0) write(r0.x, s0);
+      if (gl == 0 && r1.x >= 0) write(r1.x, s1);
+    } else {
+      // two nodes per lane: a and a + 32 of a run of 64
+      const int64_t a0 = (u - e3) * 64 + lane, a1 = a0 + 32;
+      int32_t b0 = 0, f0 = 0, b1 = 0, f1 = 0;  // f: end, or the start when not tiny
+      if (a0 < n) {
+        b0 = ptr[a0];
+        f0 = ptr[a0 + 1];
+      }
+      if (a1 < n) {
+        b1 = ptr[a1];
+        f1 = ptr[a1 + 1];
+      }
+      const bool t0 = a0 < n && f0 - b0 <= kTiny, t1 = a1 < n && f1 - b1 <= kTiny;
+      if (!t0) f0 = b0;
+      if (!t1) f1 = b1;
+      T v0[kTiny], v1[kTiny];
+#pragma unroll
+      for (int j = 0; j < kTiny; ++j) {
+        v0[j] = (b0 + j < f0) ? val(b0 + j) : (T)0;
+        v1[j] = (b1 + j < f1) ? val(b1 + j) : (T)0;
+      }
+      if (t0) write((int32_t)a0, (v0[0] + v0[1]) + (v0[2] + v0[3]));
+      if (t1) write((int32_t)a1, (v1[0] + v1[1]) + (v1[2] + v1[3]));
     }
   }
 }
@@ -362,9 +352,9 @@ __global__ void k_classify(const int32_t *__restrict__ ptr, int32_t n, Classes C
        a += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = ptr[a], e = ptr[a + 1], len = e - b;
     if (len > kTiny && len <= kShort) {
-      C.small[atomicAdd(&cnt[3], 1)] = (int32_t)a;
+      C.small[atomicAdd(&cnt[3], 1)] = make_int4((int32_t)a, b, e, 0);
     } else if (len > kShort && len <= kMid) {
-      C.mid[atomicAdd(&cnt[0], 1)] = (int32_t)a;
+      C.mid[atomicAdd(&cnt[0], 1)] = make_int4((int32_t)a, b, e, 0);
     } else if (len > kMid) {
       const int32_t l = atomicAdd(&cnt[1], 1);
       const int32_t c = (len + kChunk - 1) / kChunk;
@@ -471,48 +461,36 @@ static int grid_of(int64_t work, int per_block, int dev, int per_sm = 8) {
   return (int)(want < 1 ? 1 : (want > cap ? cap : want));
 }
 
-// Segmented reduction over the lists of ptr (size classes C) in one launch of
-// up to 8 x SMs blocks, split between the classes by their estimated rounds
-// of work per block: a chunk item about three rounds of a block, a mid list
-// about two rounds of a warp (8 per block), a small list one round of an
-// 8-lane group (32 per block), any node one round of a thread (256 per block).
+// Segmented reduction over the lists of ptr (size classes C): one launch of
+// at most 8 blocks of 8 warps per SM (all resident).
 template <class T, class V, class W>
-static void segmented(const int32_t *ptr, int32_t n, const Classes &C, V val, W write,
-                      double *part, int32_t *done, int dev, cudaStream_t st) {
-  const int64_t blocks = (int64_t)sm_count(dev) * 8;
-  const double w_long = 3.0 * C.n_items, w_mid = 2.0 * C.n_mid / 8.0,
-               w_small = C.n_small / 32.0, w_tiny = n / 256.0;
-  const double w_all = w_long + w_mid + w_small + w_tiny;
-  auto share = [&](double w, int64_t cap) -> int64_t {
-    if (cap <= 0) return 0;
-    int64_t b = (int64_t)(blocks * w / w_all);
-    if (b < 1) b = 1;
-    return b > cap ? cap : b;
-  };
-  const int64_t nb_long = share(w_long, C.n_items);
-  const int64_t nb_mid = share(w_mid, ((int64_t)C.n_mid + 7) / 8);
-  const int64_t nb_small = share(w_small, ((int64_t)C.n_small + 31) / 32);
-  const int64_t nb_tiny = share(w_tiny, ((int64_t)n + 255) / 256);
-  k_seg<T><<<(int)(nb_long + nb_mid + nb_small + nb_tiny), kChunkBlock, 0, st>>>(
-      ptr, n, C, val, write, reinterpret_cast<T *>(part), done, (int32_t)nb_long,
-      (int32_t)nb_mid, (int32_t)nb_small);
+static void segmented(srk_linear_ctx *x, const int32_t *ptr, const Classes &C, V val, W write,
+                      cudaStream_t st) {
+  const int64_t units = (int64_t)C.n_items + C.n_mid + ((int64_t)C.n_small + 7) / 8 +
+                        ((int64_t)x->n + 63) / 64;
+  const int warps = kSegBlock / 32;
+  int64_t blocks = (units + warps - 1) / warps;
+  const int64_t cap = (int64_t)sm_count(x->device) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_seg<T><<<(int)blocks, kSegBlock, 0, st>>>(ptr, x->n, C, val, write,
+                                              reinterpret_cast<T *>(x->part), x->done);
 }
 
 // out = alpha add + beta P^T in (columns of stride S; gather along in-lists).
-static void gather_t(const srk_linear_ctx *x, const float *in, const float *add, float alpha,
+static void gather_t(srk_linear_ctx *x, const float *in, const float *add, float alpha,
                      float beta, float *out, cudaStream_t st) {
   const int32_t S = x->L + 1;
-  segmented<float>(x->g->row_ptr, x->n, x->topo->in, GatherVal{x->g->col, x->Pe, in, S},
-                   WriteAxpy{out, add, alpha, beta, S}, x->part, x->done, x->device, st);
+  segmented<float>(x, x->g->row_ptr, x->topo->in, GatherVal{x->g->col, x->Pe, in, S},
+                   WriteAxpy{out, add, alpha, beta, S}, st);
 }
 
 // out = scale P in (columns of stride S; gather along the transpose's out-lists).
-static void gather_p(const srk_linear_ctx *x, const float *in, float scale, float *out,
+static void gather_p(srk_linear_ctx *x, const float *in, float scale, float *out,
                      cudaStream_t st) {
   const int32_t S = x->L + 1;
-  segmented<float>(x->topo->out_ptr, x->n, x->topo->out,
-                   GatherVal{x->topo->t_a, x->PeT, in, S}, WriteAxpy{out, nullptr, 0.0f, scale, S},
-                   x->part, x->done, x->device, st);
+  segmented<float>(x, x->topo->out_ptr, x->topo->out, GatherVal{x->topo->t_a, x->PeT, in, S},
+                   WriteAxpy{out, nullptr, 0.0f, scale, S}, st);
 }
 
 // Capacities of the class arrays of one direction.
@@ -523,12 +501,16 @@ static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Carves the class arrays of one direction from p (sizes only when p is
 // null); returns the bytes used.
 static size_t class_layout(Classes *C, char *p, int32_t n, int64_t m) {
-  const size_t sizes[8] = {(size_t)n,    (size_t)n,         items_max(m),     items_max(m),
-                           items_max(m), items_max(m),      long_lists_max(m), long_lists_max(m)};
-  int32_t **dst[8] = {&C->small,     &C->mid,        &C->item_node,  &C->item_beg,
-                      &C->item_end,  &C->item_long,  &C->long_first, &C->long_count};
   size_t off = 0;
-  for (int i = 0; i < 8; ++i) {
+  for (int4 **rec : {&C->small, &C->mid}) {  // at most n lists each
+    if (p) *rec = reinterpret_cast<int4 *>(p + off);
+    off += up256(sizeof(int4) * (size_t)n);
+  }
+  const size_t sizes[6] = {items_max(m), items_max(m),      items_max(m),
+                           items_max(m), long_lists_max(m), long_lists_max(m)};
+  int32_t **dst[6] = {&C->item_node, &C->item_beg,   &C->item_end,
+                      &C->item_long, &C->long_first, &C->long_count};
+  for (int i = 0; i < 6; ++i) {
     if (p) *dst[i] = reinterpret_cast<int32_t *>(p + off);
     off += up256(sizeof(int32_t) * sizes[i]);
   }
@@ -746,8 +728,7 @@ extern "C" int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s
   cudaMemsetAsync(x->done, 0, sizeof(int32_t) * cap, st);
   cudaMemsetAsync(x->bad, 0, sizeof(int), st);
   // W_a (FP32 sums in a fixed order), then P in in-list and in out-list order
-  segmented<float>(g->row_ptr, g->n, topo->in, WeightVal{edge_w}, WriteVec{x->Wa}, x->part,
-                   x->done, dev, st);
+  segmented<float>(x, g->row_ptr, topo->in, WeightVal{edge_w}, WriteVec{x->Wa}, st);
   if (g->m > 0) {
     k_lin_pe<<<gm, 256, 0, st>>>(edge_w, topo->erow, x->Wa, g->m, x->Pe, x->bad);
     k_gather_f32<<<gm, 256, 0, st>>>(x->Pe, topo->t_e, g->m, x->PeT);
@@ -815,8 +796,7 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
       // G_e into grad_w, T_a = sum G_e P_e per in-list, then the normalisation
       k_lin_edge_G<<<gm, 256, 0, st>>>(topo->erow, g->col, x->m, x->y, x->h, gb, yb, L, fc,
                                        grad_w);
-      segmented<float>(g->row_ptr, x->n, topo->in, DotVal{grad_w, x->Pe}, WriteVec{T}, x->part,
-                       x->done, dev, st);
+      segmented<float>(x, g->row_ptr, topo->in, DotVal{grad_w, x->Pe}, WriteVec{T}, st);
       k_lin_edge_fin<<<gm, 256, 0, st>>>(topo->erow, x->m, T, x->Wa, grad_w);
     } else {
       cudaMemsetAsync(grad_w, 0, sizeof(float) * (size_t)x->m, st);  // s_vec = D e_s
