@@ -60,7 +60,8 @@ def parse():
                     help="approximate CPU time budget of the oracle baseline")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-probe", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "linear", "serve"],
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "batch", "linear", "serve", "probe"],
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
@@ -172,25 +173,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def gather_probe(srk, torch, dev, n_words):
-    """Random 4-byte gather rate (loads/s) on an n_words int32 array."""
+def gather_probe(srk, torch, dev, n_words, cache_ops=(0,)):
+    """Random 4-byte gather rate (loads/s) on an n_words int32 array, for each
+    PTX cache operator in cache_ops (SRK_PROBE_*); returns a list of rates."""
     data = torch.randint(0, 1 << 30, (n_words,), dtype=torch.int32, device=dev)
     sink = torch.zeros(1, dtype=torch.int64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    srk.srk_probe_gather(data, 64, 1, sink)
-    torch.cuda.synchronize()
-    iters, rate = 500, 0.0
-    for rep in range(3):
-        ev[0].record()
-        loads = srk.srk_probe_gather(data, iters, 11 + rep, sink)
-        ev[1].record()
-        ev[1].synchronize()
-        t = ev[0].elapsed_time(ev[1]) / 1e3
-        rate = max(rate, loads / t) if rep else rate
-        if rep == 0:
-            iters = max(100, int(iters * 0.05 / t))
+    rates = []
+    for op in cache_ops:
+        srk.srk_probe_gather(data, 64, 1, sink, cache_op=op)
+        torch.cuda.synchronize()
+        iters, rate = 500, 0.0
+        for rep in range(3):
+            ev[0].record()
+            loads = srk.srk_probe_gather(data, iters, 11 + rep, sink, cache_op=op)
+            ev[1].record()
+            ev[1].synchronize()
+            t = ev[0].elapsed_time(ev[1]) / 1e3
+            rate = max(rate, loads / t) if rep else rate
+            if rep == 0:
+                iters = max(100, int(iters * 0.05 / t))
+        rates.append(rate)
     del data
-    return rate
+    return rates
 
 
 def kernel_source_sha256():
@@ -302,6 +307,34 @@ def run_batch(args, rank, world):
             "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
     print(json.dumps(line), flush=True)
     g.close()
+    return 0
+
+
+def run_probe(args, rank, world):
+    """The random-gather ceiling itself: srk_probe_gather_ex over arrays from
+    16 KB (L1-resident) to 4 GB (HBM) with each PTX cache operator; one line
+    of loads/s per (size, operator)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as srk
+    ops = {"default": srk.SRK_PROBE_DEFAULT, "cg": srk.SRK_PROBE_CG,
+           "nc": srk.SRK_PROBE_NC, "ca": srk.SRK_PROBE_CA}
+    sizes_mb = [0.015625, 0.25, 4, 16, 64, 96, 128, 256, 1024, 4096]
+    table = {}
+    for mb in sizes_mb:
+        words = int(mb * (1 << 20)) // 4
+        rates = gather_probe(srk, torch, dev, words, tuple(ops.values()))
+        table["%g MB" % mb] = dict(zip(ops.keys(), rates))
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    line = {"metric": "random 4-byte gather loads/s by array size and cache operator",
+            "workload": "gather_probe_sweep", "unit": "loads/s", "sms": sm,
+            "value": table["64 MB"]["default"], "higher_is_better": True,
+            "table": table, "note": "full-occupancy grid, 4 independent loads per thread "
+                                    "per round, LCG indices; best of 2 timed runs"}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -492,6 +525,8 @@ def main():
         return run_linear(args, rank, world) if rank == 0 else 0
     if args.workload == "serve":
         return run_serve(args, rank, world) if rank == 0 else 0
+    if args.workload == "probe":
+        return run_probe(args, rank, world) if rank == 0 else 0
 
     import torch
     if not torch.cuda.is_available():
@@ -607,10 +642,16 @@ def main():
                 "kernel_share_of_query": float(np.sum(k_ms) / np.sum(q_ms))}
     gather = None
     if not args.skip_probe:
-        l2_rate = gather_probe(srk, torch, dev, n + m)          # graph-sized array
-        hbm_rate = gather_probe(srk, torch, dev, 1 << 30)       # 4 GB array
+        ops = (srk.SRK_PROBE_DEFAULT, srk.SRK_PROBE_CG, srk.SRK_PROBE_NC, srk.SRK_PROBE_CA)
+        by_op = gather_probe(srk, torch, dev, n + m, ops)       # graph-sized array
+        l2_rate = by_op[0]
+        hbm_rate = gather_probe(srk, torch, dev, 1 << 30)[0]    # 4 GB array
+        l1_rate = gather_probe(srk, torch, dev, 1 << 12)[0]     # 16 KB array (L1 hits)
         gather = {"probe_gathers_per_s_graph_sized": l2_rate,
                   "probe_gathers_per_s_4GB": hbm_rate,
+                  "probe_gathers_per_s_16KB": l1_rate,
+                  "probe_graph_sized_by_cache_op": dict(zip(("default", "cg", "nc", "ca"),
+                                                            by_op)),
                   "kernel_steps_per_s": target_steps_per_s,
                   "frac_of_graph_sized_probe": target_steps_per_s / l2_rate,
                   "note": "one scattered 4-byte adjacency read per target-walk step; "
@@ -635,6 +676,10 @@ def main():
                        "parallelism": "sources sharded over ranks" if world > 1 else "1 GPU"},
             "walk_steps_per_s": steps_per_s,
             "target_steps_per_query": tgt_steps / args.steps,
+            "query_ms": {"best": float(np.min(q_ms)), "median": float(np.median(q_ms)),
+                         "max": float(np.max(q_ms)),
+                         "note": "per-query CUDA-event times on this rank; sources differ "
+                                 "in work (active pairs per target)"},
             "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "e2e": e2e, "clocks": clk,
             "gpu_launches": 9 * args.steps,

@@ -279,6 +279,19 @@ int srk_probe_gather(const int32_t *data, int64_t n, int64_t iters, uint32_t see
                      unsigned long long *sink, int64_t *loads, void *cuda_stream);
 
 /*
+ * srk_probe_gather_ex -- srk_probe_gather with the PTX cache operator of the
+ * loads chosen by `cache_op` (one of SRK_PROBE_*), to show whether a cache
+ * hint changes the random-gather ceiling.  SRK_EINVAL for an unknown value.
+ */
+#define SRK_PROBE_DEFAULT 0  /* ld.global */
+#define SRK_PROBE_CG      1  /* ld.global.cg: cache in L2, not L1 */
+#define SRK_PROBE_NC      2  /* ld.global.nc: read-only data path */
+#define SRK_PROBE_CA      3  /* ld.global.ca: cache at all levels */
+int srk_probe_gather_ex(const int32_t *data, int64_t n, int64_t iters, uint32_t seed,
+                        int32_t cache_op, unsigned long long *sink, int64_t *loads,
+                        void *cuda_stream);
+
+/*
  * Query server (no counterpart in the paper; the serving configuration):
  * resident graphs, memory-based admission, worker threads with one CUDA
  * stream each, latency statistics.

@@ -23,6 +23,7 @@ __all__ = [
     "SrkError", "SrkOpts", "SrkStats", "Graph",
     "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
     "srk_multi_source", "srk_single_source_noalloc", "srk_probe_gather",
+    "srk_probe_gather_ex", "SRK_PROBE_DEFAULT", "SRK_PROBE_CG", "SRK_PROBE_NC", "SRK_PROBE_CA",
     "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free", "LinearContext",
     "LinearSimRank", "linear_simrank", "SrkServerReport", "Server",
     "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
@@ -36,6 +37,7 @@ __all__ = [
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
 SRK_DEVICE_PTRS, SRK_VALIDATE = 1, 2
 SRK_OPT_NO_GRAPH, SRK_OPT_WARMUP_RULE, SRK_OPT_LITERAL_SHUFFLE = 1, 2, 4
+SRK_PROBE_DEFAULT, SRK_PROBE_CG, SRK_PROBE_NC, SRK_PROBE_CA = 0, 1, 2, 3
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
 SRK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -85,6 +87,8 @@ _lib.srk_multi_source.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double,
                                   _vp, _vp, _vp]
 _lib.srk_probe_gather.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
                                   _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+_lib.srk_probe_gather_ex.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
+                                     ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
 _lib.srk_linear_fwd.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                 _vp, ctypes.POINTER(_vp), _vp]
 _lib.srk_linear_bwd.argtypes = [_vp, _vp, _vp, _vp]
@@ -112,7 +116,7 @@ _lib.srk_server_destroy.argtypes = [_vp]
 _lib.srk_last_error.restype = ctypes.c_char_p
 for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
            "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
-           "srk_probe_gather", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free",
+           "srk_probe_gather", "srk_probe_gather_ex", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free",
            "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
            "srk_server_destroy"):
     getattr(_lib, _f).restype = ctypes.c_int
@@ -327,17 +331,20 @@ def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
     _check(rc)
 
 
-def srk_probe_gather(data, iters: int, seed: int, sink, stream=None) -> int:
+def srk_probe_gather(data, iters: int, seed: int, sink, stream=None,
+                     cache_op: int = 0) -> int:
     """Enqueue the random-gather probe over ``data`` (device int32 tensor);
-    returns the number of 4-byte loads it issues.  ``sink``: device int64[1]."""
+    returns the number of 4-byte loads it issues.  ``sink``: device int64[1].
+    ``cache_op``: one of SRK_PROBE_* (``srk_probe_gather_ex``)."""
     dp, d_dev, k1 = _ptr(data, "int32")
     sp, s_dev, k2 = _ptr(sink, "uint64")
     if not (d_dev and s_dev):
         raise ValueError("data and sink must be device tensors")
     n = data.numel()
     loads = ctypes.c_int64()
-    rc = _lib.srk_probe_gather(dp, int(n), int(iters), int(seed) & 0xFFFFFFFF, sp,
-                               ctypes.byref(loads), _stream_handle(stream))
+    rc = _lib.srk_probe_gather_ex(dp, int(n), int(iters), int(seed) & 0xFFFFFFFF,
+                                  int(cache_op), sp, ctypes.byref(loads),
+                                  _stream_handle(stream))
     del k1, k2
     _check(rc)
     return loads.value
@@ -361,6 +368,12 @@ class LinearContext:
             self.free()
         except Exception:
             pass
+
+
+def srk_probe_gather_ex(data, iters: int, seed: int, cache_op: int, sink, stream=None) -> int:
+    """``srk_probe_gather`` with the loads' PTX cache operator ``cache_op``
+    (SRK_PROBE_DEFAULT, _CG, _NC or _CA)."""
+    return srk_probe_gather(data, iters, seed, sink, stream=stream, cache_op=cache_op)
 
 
 def srk_linear_fwd(g: Graph, edge_w, s: int, c: float, L: int, s_out, *,

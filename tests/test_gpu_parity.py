@@ -418,3 +418,20 @@ def test_walk_count_near_the_limit_sampled_targets(srk):
     targets = np.array([0, 1, 2, 500, 998, 999], dtype=np.int64)
     ref = oracle_query(rp, col, 3, 0.1, 21, targets=targets, z_override=z, L_override=L)
     assert_parity(gpu, ref, targets)
+
+
+def test_gather_probe_cache_operators(srk):
+    # the measurement utility: every cache operator issues the announced loads
+    # and finishes; an unknown operator is refused before any launch
+    import torch
+    dev = torch.device("cuda:0")
+    data = torch.arange(1 << 16, dtype=torch.int32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    counts = []
+    for op in (srk.SRK_PROBE_DEFAULT, srk.SRK_PROBE_CG, srk.SRK_PROBE_NC, srk.SRK_PROBE_CA):
+        counts.append(srk.srk_probe_gather_ex(data, 8, 3, op, sink))
+    torch.cuda.synchronize()
+    assert len(set(counts)) == 1 and counts[0] > 0 and counts[0] % (256 * 8 * 4) == 0
+    with pytest.raises(srk.SrkError) as e:
+        srk.srk_probe_gather_ex(data, 8, 3, 7, sink)
+    assert e.value.code == srk.SRK_EINVAL
