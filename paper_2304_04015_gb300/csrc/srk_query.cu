@@ -184,9 +184,25 @@ k_pairs(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ kdraw,
 
 // Hit-table geometry: pairs sorted by cap, descending.  Row i (i = 1..L) has
 // cnt[i] = #pairs with cap >= i entries and starts at R[i].
-__global__ void k_rows(int L, int32_t *__restrict__ small_base) {
+// Also finds [act_lo, act_hi), the part of the ascending active-target list
+// `act` inside [u_begin, u_end): the target kernel's work counter starts at
+// act_lo, and act_hi is stored in the word after it.
+__global__ void k_rows(int L, int32_t *__restrict__ small_base, const int32_t *__restrict__ act,
+                       int32_t n_act, int32_t n, int32_t u_begin, int32_t u_end) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Small sm = small_view(small_base);
+  int32_t *bounds = reinterpret_cast<int32_t *>(sm.ctr + 2);  // counter, act_hi
+  auto lower_bound = [&](int32_t v) {  // first index with act[index] >= v
+    int32_t lo = 0, hi = n_act;
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if (act[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  bounds[0] = u_begin == 0 ? 0 : lower_bound(u_begin);
+  bounds[1] = u_end == n ? n_act : lower_bound(u_end);
   int32_t c = 0;
   sm.cnt[L + 1] = 0;
   for (int i = L; i >= 1; --i) {
@@ -268,7 +284,8 @@ struct TargetArgs {
   unsigned long long *wsums;
   uint32_t *steps_per_target;
   unsigned long long *steps_total;
-  int32_t *target_counter;  // zeroed before the launch
+  int32_t *target_counter;  // next index into act (from act_lo), then act_hi
+  const int32_t *act;       // the targets with in-neighbours, ascending
   int32_t u_begin, u_end;   // targets computed: [u_begin, u_end)
   int32_t N_tot;            // literal mode: the permutation's domain
 };
@@ -311,11 +328,20 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   S.s = (uint32_t)A.s;
   const FeistelShape fs = feistel_shape(A.N_tot);
   unsigned long long warp_steps = 0;
+  // the active targets act[counter .. act_hi) (k_rows set the counter to the
+  // range's first index and act_hi beside it); the outputs of the others
+  // were cleared before the launch, and s's score is 1
+  if (blockIdx.x == 0 && threadIdx.x == 0 && A.s >= A.u_begin && A.s < A.u_end)
+    A.scores[A.s] = 1.0;
+  if (S.n_pairs == 0) return;  // no pair can meet: every output is zero
   for (;;) {
-    int32_t u = 0;
-    if (lane == 0) u = A.u_begin + atomicAdd(A.target_counter, 1);
+    int32_t u = -1;
+    if (lane == 0) {
+      const int32_t q = atomicAdd(A.target_counter, 1);
+      if (q < A.target_counter[1]) u = A.act[q];
+    }
     u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= A.u_end) break;
+    if (u < 0) break;
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
     const int32_t beg_u = u + A.row_ptr[u];  // position of u
@@ -416,7 +442,17 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   k_fy_scatter<<<gN, 256, 0, st>>>(w.kdraw, w.grp_off, w.rank, w.items, N);
   k_fy_groups<<<gN, 256, 0, st>>>(w.grp_off, w.items, w.first, w.succ, N);
   k_pairs<<<gN, 256, 0, st>>>(t, w.kdraw, w.first, w.succ, w.seff, w.sigma, w.small);
-  k_rows<<<1, 32, 0, st>>>(t.L, w.small);
+  k_rows<<<1, 32, 0, st>>>(t.L, w.small, g->act, g->n_act, g->n, u_begin, u_end);
+  // targets without in-neighbours have zero outputs (and s, if it is one of
+  // them, the score 1 the kernel writes): clear the range, then walk only
+  // the active targets
+  const size_t nr = (size_t)(u_end - u_begin);
+  if (nr > 0) {
+    cudaMemsetAsync(o.scores + u_begin, 0, sizeof(double) * nr, st);
+    if (o.counts) cudaMemsetAsync(o.counts + u_begin, 0, sizeof(uint32_t) * nr, st);
+    if (o.wsums) cudaMemsetAsync(o.wsums + u_begin, 0, sizeof(unsigned long long) * nr, st);
+    if (o.steps) cudaMemsetAsync(o.steps + u_begin, 0, sizeof(uint32_t) * nr, st);
+  }
   k_hit_table<<<gN, 256, 0, st>>>(t, w.sigma, w.seff, w.spos, w.small, w.pair_j,
                                   w.pair_w, w.Hc);
   TargetArgs A;
@@ -439,6 +475,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.steps_per_target = o.steps;
   A.steps_total = small_view(w.small).ctr;
   A.target_counter = reinterpret_cast<int32_t *>(small_view(w.small).ctr + 2);
+  A.act = g->act;
   A.u_begin = u_begin;
   A.u_end = u_end;
   A.N_tot = t.N_tot;
