@@ -82,8 +82,9 @@ namespace srk {
 
 // Control block of one query (int32 words): cap histogram, row sizes cnt[i]
 // (pairs with cap >= i), hit-table row offsets R[i], per-cap cursors, then
-// four uint64 counters: [0] target steps, [1] source steps, [2] target/item
-// counter, [3] spare.
+// four uint64 slots: [0] target steps, [1] source steps, [2] the target
+// kernel's work counter (low word; the batched path's item counter uses the
+// whole slot) and the end of its active-target range (high word), [3] spare.
 constexpr int kRowWords = SRK_MAX_LEN + 2;
 constexpr int kSmallWords = 4 * kRowWords;
 constexpr int kSmallBytes = 4 * kSmallWords + 32;

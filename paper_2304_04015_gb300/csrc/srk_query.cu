@@ -373,8 +373,6 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-
-
 size_t plan(const QueryTab &t, Workspace *w, char *base) {
   const size_t N = (size_t)t.N_tot;
   const size_t Ls = (size_t)(t.L > 0 ? t.L : 1);
@@ -422,8 +420,6 @@ static int target_grid(int device) {
   }
   return sm_count(device) * b;
 }
-
-
 
 // Enqueues one query on `st` with device-resident outputs `o`.  Workspace
 // `w` (already carved) must hold plan(t) bytes.
@@ -566,7 +562,6 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
   const bool d_steps = !step_counts || is_device_ptr(step_counts);
   Workspace w;
   size_t ws = plan(t, &w, nullptr);
-  const size_t ws_core = ws;
   const size_t o_scores = ws;
   if (!d_scores) ws += align_up(8 * n);
   const size_t o_counts = ws;
@@ -581,7 +576,6 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
   cudaError_t e = cudaMallocFromPoolAsync((void **)&base, ws, mp, st);
   if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
   plan(t, &w, base);
-  (void)ws_core;
   Outputs o;
   o.scores = d_scores ? scores : (double *)(base + o_scores);
   o.counts = d_counts ? meet_counts : (uint32_t *)(base + o_counts);
