@@ -246,6 +246,35 @@ def cpu_baseline(rp, col, sources, budget_s):
             "steps_per_s": steps / per_query}
 
 
+def cpu_baseline_mix(graphs_np, queries, budget_s):
+    """The oracle as it stands on a mix of queries [(graph index, s, eps)]:
+    each query on a uniform target sample grown until it takes about its
+    share of budget_s, its time scaled by n/targets; returns queries/s over
+    the mix (total scaled time / number of queries)."""
+    from oracle import sampler
+    rng = np.random.default_rng(7)
+    threads = os.cpu_count() or 1
+    share = budget_s / max(1, len(queries))
+    total, parts = 0.0, []
+    for gi, s, eps in queries:
+        rp, col = graphs_np[gi]
+        n = rp.size - 1
+        k = min(n, 256)
+        while True:
+            targets = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int32)
+            t0 = time.perf_counter()
+            sampler.run(rp, col, n, int(s), C, float(eps), QUERY_SEED, targets=targets,
+                        threads=threads)
+            dt = time.perf_counter() - t0
+            if dt >= share / 4 or k >= n:
+                break
+            k = min(n, int(k * max(2.0, share / max(dt, 1e-3) / 2)))
+        total += dt * n / k
+        parts.append("n=%d s=%d eps=%g: %d targets %.1f s" % (n, s, eps, k, dt))
+    return {"value": len(queries) / total, "unit": "queries/s", "cores": threads,
+            "kind": "oracle", "sample": "; ".join(parts) + "; times scaled by n/targets"}
+
+
 def run_batch(args, rank, world):
     """Batched multi-source (srk_multi_source, one persistent launch per
     batch) against the plain path (one srk_single_source per source) on the
@@ -296,6 +325,23 @@ def run_batch(args, rank, world):
         t_plain += ev[0].elapsed_time(ev[1]) / 1e3
         same = same and bool(torch.equal(single, out[i]))
     deg = np.diff(rp)
+    peak, peak_kind = load_peaks()
+    achieved = st.target_steps * BYTES_PER_STEP / t_batch / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "kb_target_walks",
+                "peak_kind": peak_kind + " (HBM copy)", "bytes_per_unit": BYTES_PER_STEP,
+                "unit_name": "target-walk step",
+                "note": "whole batch time (the source phases are a few percent)"}
+    probe = gather_probe(srk, torch, dev, n + m)[0]
+    gather = {"probe_gathers_per_s_graph_sized": probe,
+              "kernel_steps_per_s": st.target_steps / t_batch,
+              "frac_of_graph_sized_probe": st.target_steps / t_batch / probe}
+    base = None
+    if not args.no_cpu_baseline:
+        col_h = col_d.cpu().numpy()
+        mix = [(0, sources[i], eps[i]) for i in range(min(3, k))]
+        base = cpu_baseline_mix([(rp, col_h)], mix, args.cpu_seconds)
+        del col_h
     line = {"metric": "batched multi-source queries/s (R-MAT scale %d, mixed eps)" % args.batch_scale,
             "workload": "batch_rmat%d_mixed_sources_mixed_eps" % args.batch_scale,
             "value": k / t_batch, "unit": "queries/s", "higher_is_better": True,
@@ -304,6 +350,7 @@ def run_batch(args, rank, world):
             "source_in_degrees": [int(deg[s]) for s in sources], "eps": eps,
             "target_steps": st.target_steps, "walk_steps_per_s": st.target_steps / t_batch,
             "batch_shape": st.batch_shape, "graph_gen_s": t_gen,
+            "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
     print(json.dumps(line), flush=True)
     g.close()
@@ -386,13 +433,38 @@ def run_linear(args, rank, world):
     per_pass = 12.0 * m
     fwd_bytes = 2 * L * per_pass
     bwd_bytes = 2 * L * per_pass + m * (8 + 4 * 2 * L)
+    peak, peak_kind = load_peaks()
+    achieved = (fwd_bytes + bwd_bytes) * args.steps / t / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "forward+backward (all kernels; the k_seg gathers are ~75 % of "
+                          "device time in the launch list)",
+                "peak_kind": peak_kind + " (HBM copy)",
+                "bytes_per_unit": fwd_bytes + bwd_bytes, "unit_name": "forward+backward"}
+    base = None
+    if not args.no_cpu_baseline:
+        from oracle import linear
+        import torch as _t
+        w64 = w.cpu().numpy().astype(np.float64)
+        g64 = lw.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 1 or (time.perf_counter() - t0 < args.cpu_seconds / 2 and reps < 3):
+            linear.grad(rp, col, w64, n, srcs[reps % len(srcs)], C, L, g64)
+            reps += 1
+        dt = (time.perf_counter() - t0) / reps
+        base = {"value": 1.0 / dt, "unit": "fwd+bwd/s", "cores": _t.get_num_threads(),
+                "kind": "oracle",
+                "sample": "%d full forward+backward passes of the oracle (FP64 sparse "
+                          "products and reverse mode)" % reps}
     line = {"metric": "linearised SimRank forward+backward per second (R-MAT 18, L=10)",
             "workload": "linear_rmat18_L10_lognormal_weights", "value": args.steps / t,
             "unit": "fwd+bwd/s", "higher_is_better": True, "n": n, "m": m,
             "fwd_ms": float(np.mean(fwd_ms)), "bwd_ms": float(np.mean(bwd_ms)),
             "fwd_GBps_streamed": fwd_bytes / (np.mean(fwd_ms) / 1e3) / 1e9,
             "bwd_GBps_streamed": bwd_bytes / (np.mean(bwd_ms) / 1e3) / 1e9,
-            "dtype": "f32", "steps": args.steps, "warmup": args.warmup}
+            "dtype": "f32", "steps": args.steps, "warmup": args.warmup,
+            "roofline": roofline, "cpu_baseline": base}
     print(json.dumps(line), flush=True)
     g.close()
     return 0
@@ -413,7 +485,7 @@ def run_serve(args, rank, world):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2304_04015_gb300 as srk
-    graphs, sizes = [], []
+    graphs, sizes, hosts = [], [], []
     for scale in (16, 20, 23):
         if scale <= 20:
             rp, col = rmat_in_csr(scale, seed=GRAPH_SEED)
@@ -422,6 +494,7 @@ def run_serve(args, rank, world):
             rp_d, col_d = rmat_in_csr_torch(scale, seed=GRAPH_SEED, device=dev)
         graphs.append(srk.srk_graph_load(rp_d, col_d))
         sizes.append(int(rp_d.numel()) - 1)
+        hosts.append((rp_d, col_d))
     rng = np.random.default_rng(4)
     horizon = args.serve_seconds
     t_arr = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * horizon * 1.2) + 16))
@@ -459,6 +532,21 @@ def run_serve(args, rank, world):
         ev[1].record()
         ev[1].synchronize()
         t_plain += ev[0].elapsed_time(ev[1]) / 1e3
+    peak, peak_kind = load_peaks()
+    achieved = st.target_steps * BYTES_PER_STEP / st.wall_s / 1e9 if st.wall_s else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_target_walks",
+                "peak_kind": peak_kind + " (HBM copy)", "bytes_per_unit": BYTES_PER_STEP,
+                "unit_name": "target-walk step",
+                "note": "over the serving run's wall time (includes idle gaps)"}
+    base = None
+    if not args.no_cpu_baseline and admitted:
+        mix = [reqs[k] for k in admitted[:6]]
+        need = sorted({gi for gi, _, _ in mix})
+        graphs_np = [None] * 3
+        for gi in need:
+            graphs_np[gi] = (hosts[gi][0].cpu().numpy(), hosts[gi][1].cpu().numpy())
+        base = cpu_baseline_mix(graphs_np, mix, args.cpu_seconds)
     line = {"metric": "served single-source SimRank queries/s and latency (R-MAT 16/20/23)",
             "workload": "serve_rmat16_20_23_poisson", "value": st.queries_per_s,
             "unit": "queries/s", "higher_is_better": True,
@@ -471,7 +559,7 @@ def run_serve(args, rank, world):
             "workers": args.serve_workers, "latency_target_ms": args.serve_target_ms,
             "submit_loop_s": t_submit_end,
             "plain_one_at_a_time_queries_per_s": len(admitted) / t_plain if t_plain else None,
-            "graph_nodes": sizes}
+            "graph_nodes": sizes, "roofline": roofline, "cpu_baseline": base}
     print(json.dumps(line), flush=True)
     for g in graphs:
         g.close()
