@@ -1,0 +1,123 @@
+"""Parity at the full sizes of the batching and serving workloads, on sampled
+targets the oracle computes one by one.
+
+* Batching: R-MAT scale 24 (16.8M nodes, ~263M edges, drawn on the device),
+  the first three sources of the 4096-source batching list (a top in-degree,
+  a median in-degree and a zero in-degree node) with their own eps from
+  {0.05, 0.02, 0.01}, run through srk_multi_source as the benchmark runs
+  them; counts and scores bit-exact on 24 sampled targets per source.
+* Serving: R-MAT scales 16, 20 and 23 resident in one server; two requests
+  per graph with host score buffers; scores bit-exact on 24 sampled targets
+  per request.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+C = 0.6
+SEED = 20240405
+
+
+@pytest.fixture(scope="module")
+def srk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as m
+    return m
+
+
+def sampled_targets(n, k, seed, must=()):
+    rng = np.random.default_rng(seed)
+    t = set(int(x) for x in rng.choice(n, size=k, replace=False))
+    t.update(int(x) for x in must)
+    return np.array(sorted(t), dtype=np.int64)
+
+
+def test_batching_workload_rmat24_sampled_targets(srk):
+    import torch
+    from oracle import sampler
+    from srk_inputs import mixed_eps, mixed_sources, rmat_in_csr_torch
+    dev = torch.device("cuda:0")
+    rp_d, col_d = rmat_in_csr_torch(24, seed=1, device=dev)
+    rp = rp_d.cpu().numpy()
+    n = rp.size - 1
+    all_src = mixed_sources(rp, 4096, seed=3)
+    all_eps = mixed_eps(4096, seed=3)
+    third = 4096 // 3
+    pick = [0, third, 2 * third]  # first source of each group, as the benchmark orders them
+    sources = [int(all_src[i]) for i in pick]
+    eps = [float(all_eps[i]) for i in pick]
+    deg = np.diff(rp)
+    assert deg[sources[0]] > 1000 and deg[sources[2]] == 0
+    g = srk.srk_graph_load(rp_d, col_d)
+    try:
+        scores = torch.empty((3, n), dtype=torch.float64, device=dev)
+        counts = torch.empty((3, n), dtype=torch.int32, device=dev)
+        srk.srk_multi_source(g, sources, C, eps, SEED, scores, counts)
+        torch.cuda.synchronize()
+        col = col_d.cpu().numpy()
+        hubs = np.argpartition(-deg, 12)[:12]  # targets whose walks meet often
+        met = 0
+        for i, (s, e) in enumerate(zip(sources, eps)):
+            tg = sampled_targets(n, 24, 100 + i, must=hubs)
+            ref = sampler.run(rp, col, n, s, C, e, SEED, targets=tg.astype(np.int32))
+            got_c = counts[i, tg].cpu().numpy().view(np.uint32)
+            got_s = scores[i, tg].cpu().numpy()
+            assert np.array_equal(got_c, ref.count)
+            assert np.array_equal(got_s, ref.scores)
+            met += int(ref.count.sum())
+        assert met > 0
+        # the zero in-degree source: e_s exactly
+        row = scores[2]
+        assert float(row[sources[2]]) == 1.0 and int(torch.count_nonzero(row)) == 1
+        assert int(counts[0].sum()) > 0
+    finally:
+        g.close()
+
+
+def test_serving_workload_rmat16_20_23_sampled_targets(srk):
+    import torch
+    from oracle import sampler
+    from srk_inputs import rmat_in_csr, rmat_in_csr_torch
+    dev = torch.device("cuda:0")
+    hosts, handles = [], []
+    try:
+        for scale in (16, 20, 23):
+            if scale <= 20:
+                rp, col = rmat_in_csr(scale, seed=1)
+                rp_d, col_d = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
+            else:
+                rp_d, col_d = rmat_in_csr_torch(scale, seed=1, device=dev)
+                rp, col = rp_d.cpu().numpy(), col_d.cpu().numpy()
+            handles.append(srk.srk_graph_load(rp_d, col_d))
+            hosts.append((rp, col))
+        rng = np.random.default_rng(11)
+        reqs = []
+        with srk.srk_server_create(handles, mem_budget=8 << 30, n_workers=3) as srv:
+            for gi in (0, 1, 2, 0, 1, 2):
+                rp, col = hosts[gi]
+                n = rp.size - 1
+                active = np.flatnonzero(np.diff(rp) > 0)
+                s = int(rng.choice(active))
+                e = 0.05 if gi == 2 else 0.02
+                buf = np.full(n, -1.0)
+                assert srk.srk_server_submit(srv, gi, s, C, e, SEED + len(reqs), buf)
+                reqs.append((gi, s, e, SEED + len(reqs), buf))
+            srk.srk_server_drain(srv)
+            st = srk.srk_server_stats(srv)
+            assert st.completed == 6 and st.failed == 0
+        met = 0
+        for k, (gi, s, e, seed, buf) in enumerate(reqs):
+            rp, col = hosts[gi]
+            n = rp.size - 1
+            hubs = np.argpartition(-np.diff(rp), 12)[:12]
+            tg = sampled_targets(n, 24, 200 + k, must=hubs)
+            ref = sampler.run(rp, col, n, s, C, e, seed, targets=tg.astype(np.int32))
+            assert np.array_equal(buf[tg], ref.scores)
+            assert buf[s] == 1.0
+            met += int(ref.count.sum())
+        assert met > 0
+    finally:
+        for h in handles:
+            h.close()
