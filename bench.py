@@ -65,6 +65,8 @@ def parse():
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--layout", default=None, choices=["narrow", "wide"],
+                    help="adjacency entry layout (default: chosen by graph size)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-budget-mb", type=int, default=1024)
@@ -302,7 +304,7 @@ def run_batch(args, rank, world):
     pick = order[:args.batch_sources]
     sources = [int(all_src[i]) for i in pick]
     eps = [float(all_eps[i]) for i in pick]
-    g = srk.srk_graph_load(rp_d, col_d)
+    g = srk.srk_graph_load(rp_d, col_d, layout=args.layout)
     k = len(sources)
     out = torch.empty((k, n), dtype=torch.float64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -350,6 +352,7 @@ def run_batch(args, rank, world):
             "source_in_degrees": [int(deg[s]) for s in sources], "eps": eps,
             "target_steps": st.target_steps, "walk_steps_per_s": st.target_steps / t_batch,
             "batch_shape": st.batch_shape, "graph_gen_s": t_gen,
+            "adjacency": args.layout or ("wide" if n + m > (1 << 27) else "narrow"),
             "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
     print(json.dumps(line), flush=True)
@@ -492,7 +495,7 @@ def run_serve(args, rank, world):
             rp_d, col_d = torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev)
         else:
             rp_d, col_d = rmat_in_csr_torch(scale, seed=GRAPH_SEED, device=dev)
-        graphs.append(srk.srk_graph_load(rp_d, col_d))
+        graphs.append(srk.srk_graph_load(rp_d, col_d, layout=args.layout))
         sizes.append(int(rp_d.numel()) - 1)
         hosts.append((rp_d, col_d))
     rng = np.random.default_rng(4)
@@ -640,7 +643,7 @@ def main():
 
     rp_d = torch.from_numpy(rp).to(dev)
     col_d = torch.from_numpy(col).to(dev)
-    g = srk.srk_graph_load(rp_d, col_d)
+    g = srk.srk_graph_load(rp_d, col_d, layout=args.layout)
     stream = torch.cuda.current_stream(dev)
     scores = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -757,6 +760,7 @@ def main():
                        "(0.57,0.19,0.19,0.05), dedup, no self-loops, seed %d" % GRAPH_SEED,
                        "n": n, "m": m, "c": C, "eps": EPS, "sources": N_SOURCES,
                        "source_seed": SOURCE_SEED, "query_seed": QUERY_SEED,
+                       "adjacency": args.layout or ("wide" if n + m > (1 << 27) else "narrow"),
                        "z": stats_steps[0][4], "N_tot": stats_steps[0][2],
                        "L": int(np.floor(np.log(n) / -np.log(np.sqrt(C)))),
                        "l2": "256 MB buffer written between queries (outside the timed intervals)",

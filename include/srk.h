@@ -71,6 +71,8 @@ extern "C" {
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */
 #define SRK_VALIDATE    2  /* accepted; the CSR invariants are always checked */
+#define SRK_ADJ_NARROW  4  /* force 4-byte adjacency entries (see srk_graph_load) */
+#define SRK_ADJ_WIDE    8  /* force 8-byte adjacency entries (see srk_graph_load) */
 
 /* Upper bounds of this build. */
 #define SRK_MAX_LEN   255          /* largest truncation length L */
@@ -122,6 +124,14 @@ typedef struct srk_opts {
  *                  are borrowed; the caller keeps them alive and unchanged
  *                  until srk_graph_free.  Otherwise they are host arrays and
  *                  are copied.  SRK_VALIDATE is accepted and implied.
+ *                  SRK_ADJ_NARROW / SRK_ADJ_WIDE force the layout of the
+ *                  packed adjacency the walks read (4-byte entries carrying a
+ *                  degree code of 32 - ceil(log2(n + m)) bits, or 8-byte
+ *                  entries carrying the full degree); by default 4-byte
+ *                  entries are used while n + m <= 2^27 and 8-byte entries
+ *                  beyond, where a narrow code (15 or less) would send most
+ *                  steps to a second random read.  Results do not depend on
+ *                  the layout; giving both flags is SRK_EINVAL.
  * The CSR invariants (row_ptr[0] = 0, row_ptr[n] = m, row_ptr non-decreasing,
  * 0 <= col < n) are always checked on the device before the handle is
  * returned; a violation returns SRK_EINVAL.  The walk kernels rely on them.

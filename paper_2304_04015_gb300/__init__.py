@@ -30,12 +30,12 @@ __all__ = [
     "srk_server_destroy", "srk_last_error",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
-    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_OPT_NO_GRAPH", "SRK_OPT_WARMUP_RULE", "SRK_OPT_LITERAL_SHUFFLE", "SRK_MAX_LEN",
+    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_ADJ_NARROW", "SRK_ADJ_WIDE", "SRK_OPT_NO_GRAPH", "SRK_OPT_WARMUP_RULE", "SRK_OPT_LITERAL_SHUFFLE", "SRK_MAX_LEN",
     "SRK_MAX_WALKS",
 ]
 
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
-SRK_DEVICE_PTRS, SRK_VALIDATE = 1, 2
+SRK_DEVICE_PTRS, SRK_VALIDATE, SRK_ADJ_NARROW, SRK_ADJ_WIDE = 1, 2, 4, 8
 SRK_OPT_NO_GRAPH, SRK_OPT_WARMUP_RULE, SRK_OPT_LITERAL_SHUFFLE = 1, 2, 4
 SRK_PROBE_DEFAULT, SRK_PROBE_CG, SRK_PROBE_NC, SRK_PROBE_CA = 0, 1, 2, 3
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
@@ -200,9 +200,11 @@ class Graph:
 
 
 def srk_graph_load(row_ptr, col, n: Optional[int] = None, m: Optional[int] = None,
-                   flags: Optional[int] = None, edge_w=None) -> Graph:
+                   flags: Optional[int] = None, edge_w=None,
+                   layout: Optional[str] = None) -> Graph:
     """Load an in-neighbour CSR (see ``include/srk.h``).  Device tensors are
-    borrowed (SRK_DEVICE_PTRS); host arrays are copied to the current device."""
+    borrowed (SRK_DEVICE_PTRS); host arrays are copied to the current device.
+    ``layout``: None (chosen by size), "narrow" or "wide" adjacency entries."""
     rp, rp_dev, k1 = _ptr(row_ptr, "int32")
     cl, cl_dev, k2 = _ptr(col, "int32")
     ew, ew_dev, k3 = _ptr(edge_w, "float32")
@@ -212,6 +214,8 @@ def srk_graph_load(row_ptr, col, n: Optional[int] = None, m: Optional[int] = Non
         m = col.numel() if hasattr(col, "numel") else np.asarray(col).size
     if flags is None:
         flags = SRK_DEVICE_PTRS if rp_dev else 0
+    if layout is not None:
+        flags |= {"narrow": SRK_ADJ_NARROW, "wide": SRK_ADJ_WIDE}[layout]
     if rp_dev != cl_dev or (edge_w is not None and ew_dev != rp_dev):
         raise ValueError("row_ptr, col and edge_w must all be on the device or all on the host")
     h = _vp()

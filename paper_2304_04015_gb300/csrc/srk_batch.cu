@@ -68,9 +68,10 @@ __device__ __forceinline__ int find_source(const int64_t *off, int k, int64_t g)
   }
 
 // a2: source walks and Fisher-Yates draws of every source of the batch.
+template <bool kWide>
 __global__ void __launch_bounds__(256) kb_source_walks(const __grid_constant__ BatchArgs A) {
   const RoundKeys rk = round_keys(A.key0, A.key1);
-  const Adj G = make_adj(A.adj, A.pos_bits);
+  const auto G = adj_view<kWide>(A.adj, A.pos_bits);
   SRK_BATCH_LOOP(A, {
     const QueryTab &t = *S_.tab;
     const uint32_t s = (uint32_t)S_.s;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) kb_source_walks(const __grid_constant__ B
     S_.w.grp_cnt[r_] = 0;
     S_.w.kdraw[r_] = (r_ >= 1) ? fy_draw(rk, s, r_) : 0;
     const int len = stratum_of(t.P, S_.L, r_);
-    const int eff = source_walk(rk, G, s, p_s, G.adj[p_s], r_, len,
+    const int eff = source_walk(rk, G, s, p_s, header_deg(G, p_s), r_, len,
                                 S_.w.spos + (int64_t)r_ * Ls);
     S_.w.seff[r_] = eff;
     atomicAdd(small_view(S_.w.small).ctr + 1, (unsigned long long)eff);
@@ -238,7 +239,7 @@ __global__ void kb_prefill(const BatchSrc *__restrict__ src, int32_t k, int32_t 
 // list pointers and the rows cnt[0..L+2], R[0..L+2] (dynamic shared memory,
 // 2 (Lmax + 3) words per warp), so the walk loop holds no per-source state
 // in registers.
-template <int kBlock, int kMinBlocks>
+template <int kBlock, int kMinBlocks, bool kWide>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
                 int32_t n_act, const int32_t *__restrict__ act_src,
@@ -250,7 +251,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const Adj G = make_adj(A.adj, A.pos_bits);
+  const auto G = adj_view<kWide>(A.adj, A.pos_bits);
   int32_t *my_cnt = rows + (2 * wib) * row_words;
   int32_t *my_R = my_cnt + row_words;
   const int64_t n_items = (int64_t)(*n_act_src_p) * n_act;
@@ -292,7 +293,8 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
     const int32_t beg_u = u + A.row_ptr[u];
-    walk_target(rk, G, ctx[wib], (uint32_t)u, beg_u, G.adj[beg_u], lanes_below, c, W, st);
+    walk_target(rk, G, ctx[wib], (uint32_t)u, beg_u, header_deg(G, beg_u), lanes_below, c, W,
+                st);
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
       st += __shfl_xor_sync(0xffffffffu, st, off);
@@ -315,7 +317,21 @@ struct Shape {
 static const Shape kShapes[] = {{256, 8}, {512, 4}, {128, 16}, {1024, 2}, {256, 6}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-static void launch_targets(int shape, int sms, cudaStream_t st, const BatchArgs &A,
+template <bool kWide>
+static void launch_targets_t(int shape, int grid, int block, size_t smem, cudaStream_t st,
+                             const BatchArgs &A, const int32_t *act, int32_t n_act,
+                             const int32_t *act_src, const int32_t *n_act_src,
+                             unsigned long long *ctr, int64_t limit, int32_t rw) {
+  switch (shape) {
+    case 0: kb_target_walks<256, 8, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 1: kb_target_walks<512, 4, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 2: kb_target_walks<128, 16, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 3: kb_target_walks<1024, 2, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    default: kb_target_walks<256, 6, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+  }
+}
+
+static void launch_targets(bool wide, int shape, int sms, cudaStream_t st, const BatchArgs &A,
                            const int32_t *act, int32_t n_act, const int32_t *act_src,
                            const int32_t *n_act_src, unsigned long long *ctr,
                            int64_t limit, int Lmax) {
@@ -323,13 +339,12 @@ static void launch_targets(int shape, int sms, cudaStream_t st, const BatchArgs 
   const int grid = sms * sh.per_sm;
   const int32_t rw = Lmax + 3;
   const size_t smem = sizeof(int32_t) * 2 * (size_t)rw * (size_t)(sh.block / 32);
-  switch (shape) {
-    case 0: kb_target_walks<256, 8><<<grid, 256, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 1: kb_target_walks<512, 4><<<grid, 512, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 2: kb_target_walks<128, 16><<<grid, 128, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 3: kb_target_walks<1024, 2><<<grid, 1024, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    default: kb_target_walks<256, 6><<<grid, 256, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-  }
+  if (wide)
+    launch_targets_t<true>(shape, grid, sh.block, smem, st, A, act, n_act, act_src, n_act_src,
+                           ctr, limit, rw);
+  else
+    launch_targets_t<false>(shape, grid, sh.block, smem, st, A, act, n_act, act_src,
+                            n_act_src, ctr, limit, rw);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -488,7 +503,10 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       for (int32_t b = 0; b < kb; ++b)
         cudaMemsetAsync(hsrc[(size_t)b].w.small, 0, kSmallBytes, s2);
       cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * (kb + 1), s2);
-      kb_source_walks<<<gw, 256, 0, s2>>>(A);
+      if (g->wide)
+        kb_source_walks<true><<<gw, 256, 0, s2>>>(A);
+      else
+        kb_source_walks<false><<<gw, 256, 0, s2>>>(A);
       kb_fy_rank<<<gw, 256, 0, s2>>>(A);
       kb_scan<<<kb, 1024, 0, s2>>>(A);
       kb_fy_scatter<<<gw, 256, 0, s2>>>(A);
@@ -513,8 +531,8 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       for (int sh = 0; sh < kNumShapes; ++sh) {
         cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
         cudaEventRecord(t0, st);
-        launch_targets(sh, sms, st, A, g->act, g->n_act, d_act_src, d_act_src + kb, d_ctr, trial,
-                       Lmax);
+        launch_targets(g->wide, sh, sms, st, A, g->act, g->n_act, d_act_src, d_act_src + kb,
+                       d_ctr, trial, Lmax);
         cudaEventRecord(t1, st);
         float ms = 0.f;
         if (cudaEventSynchronize(t1) == cudaSuccess &&
@@ -529,8 +547,8 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     }
     auto enqueue_all = [&](cudaStream_t s2) {
       enqueue_source_side(s2);
-      launch_targets(shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb, d_ctr,
-                     INT64_MAX, Lmax);
+      launch_targets(g->wide, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
+                     d_ctr, INT64_MAX, Lmax);
     };
     if (use_graph) {
       cudaGraph_t graph = nullptr;

@@ -140,11 +140,42 @@ __device__ __forceinline__ uint32_t entry_deg(const Adj &G, uint32_t e, int32_t 
   const uint32_t code = e >> G.pb;
   return code < G.dmax ? code : G.adj[x];
 }
+__device__ __forceinline__ uint32_t header_deg(const Adj &G, int32_t p) { return G.adj[p]; }
+
+// The wide packed adjacency, for graphs whose positions need more than 27
+// bits (the degree code of a 32-bit entry would then be too small to spare
+// most steps a second random read): the same positions, with 8-byte words.
+// adj[p] = {0, |I(v)|} at a node's position p; entry k of its list,
+// adj[p + 1 + k], is {position of the k-th in-neighbour y, |I(y)|}.
+struct AdjW {
+  const uint2 *adj;
+};
+
+__host__ __device__ __forceinline__ AdjW make_adjw(const uint32_t *words) {
+  AdjW a;
+  a.adj = reinterpret_cast<const uint2 *>(words);
+  return a;
+}
+__device__ __forceinline__ uint2 adj_entry(const AdjW &G, int32_t p, uint32_t deg,
+                                           uint32_t hi, uint32_t lo) {
+  return G.adj[p + 1 + (int32_t)draw_index(hi, lo, deg)];
+}
+__device__ __forceinline__ int32_t entry_pos(const AdjW &, uint2 e) { return (int32_t)e.x; }
+__device__ __forceinline__ uint32_t entry_deg(const AdjW &, uint2 e, int32_t) { return e.y; }
+__device__ __forceinline__ uint32_t header_deg(const AdjW &G, int32_t p) { return G.adj[p].y; }
+
+// The view of a graph's adjacency words in the layout kWide names.
+template <bool kWide>
+__device__ __forceinline__ auto adj_view(const uint32_t *words, int pb) {
+  if constexpr (kWide) return make_adjw(words);
+  else return make_adj(words, pb);
+}
 
 // Source walk r of length len from the node at position p_s (degree deg_s):
 // writes the position at step i to out[i-1]; returns the steps taken.  Step
 // i draws from Philox counter ((i-1)>>1, r, s, s), words 2((i-1)&1), +1.
-__device__ __forceinline__ int source_walk(const RoundKeys &rk, const Adj &G,
+template <class GA>
+__device__ __forceinline__ int source_walk(const RoundKeys &rk, const GA &G,
                                            uint32_t s, int32_t p_s, uint32_t deg_s,
                                            int32_t r, int len, int32_t *out) {
   int32_t p = p_s;
@@ -153,7 +184,7 @@ __device__ __forceinline__ int source_walk(const RoundKeys &rk, const Adj &G,
   for (int i = 1; i <= len; ++i) {
     if (deg == 0) return i - 1;
     if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
-    const uint32_t e = adj_entry(G, p, deg, (i & 1) ? x0 : x2, (i & 1) ? x1 : x3);
+    const auto e = adj_entry(G, p, deg, (i & 1) ? x0 : x2, (i & 1) ? x1 : x3);
     p = entry_pos(G, e);
     out[i - 1] = p;
     deg = entry_deg(G, e, p);
@@ -204,7 +235,8 @@ struct PairSet {
 // All pairs of target u (position beg_u, degree deg_u > 0) walked by one
 // warp with lane refill; per-lane totals of meetings c, weight W and steps st
 // are added to the arguments (not reduced across the warp).
-__device__ __forceinline__ void walk_target(const RoundKeys &rk, const Adj &G,
+template <class GA>
+__device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
                                             const PairSet &S, uint32_t u,
                                             int32_t beg_u, uint32_t deg_u,
                                             uint32_t lanes_below, uint32_t &c,
@@ -233,7 +265,7 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const Adj &G,
       uint32_t x0, x1, x2, x3;
       philox(rk, (uint32_t)(i - 1) >> 1, j, u, S.s, x0, x1, x2, x3);
       // odd step i
-      uint32_t e = adj_entry(G, p, deg, x0, x1);
+      auto e = adj_entry(G, p, deg, x0, x1);
       int32_t x = entry_pos(G, e);
       ++st;
       if (x == S.Hc[S.R[i] + a]) {
@@ -321,8 +353,9 @@ __device__ __forceinline__ int32_t feistel_pi(const RoundKeys &rk, const Feistel
 // Philox replica t; it ends after min(l2, source cap) steps; a meeting adds
 // round(a(l1) a(l2) 2^32).  P (stratum prefix, shared memory) and a (Lemma 7
 // weights) come from the query table.
+template <class GA>
 __device__ __forceinline__ void walk_target_literal(
-    const RoundKeys &rk, const Adj &G, const PairSet &S, const FeistelShape &f,
+    const RoundKeys &rk, const GA &G, const PairSet &S, const FeistelShape &f,
     const int32_t *P, int L, const double *aw, uint32_t u,
     int32_t beg_u, uint32_t deg_u, uint32_t lanes_below, uint32_t &c,
     unsigned long long &W, uint32_t &st) {
@@ -350,7 +383,7 @@ __device__ __forceinline__ void walk_target_literal(
     if (live) {
       uint32_t x0, x1, x2, x3;
       philox(rk, (uint32_t)(i - 1) >> 1, t, u, S.s, x0, x1, x2, x3);
-      uint32_t e = adj_entry(G, p, deg, x0, x1);
+      auto e = adj_entry(G, p, deg, x0, x1);
       int32_t x = entry_pos(G, e);
       ++st;
       if (x == S.Hc[S.R[i] + a]) {

@@ -212,6 +212,31 @@ __global__ void k_build_adj_lists(const int32_t *__restrict__ row_ptr,
   }
 }
 
+// The wide layout (srk_internal.h): adj2[pos(v)] = {0, |I(v)|} and entry e
+// of list v = {pos(y), |I(y)|} for y = col[e], at the same positions.
+__global__ void k_build_adjw_heads(const int32_t *__restrict__ row_ptr, int32_t n,
+                                   uint2 *__restrict__ adj2) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    adj2[v + row_ptr[v]] = make_uint2(0u, (uint32_t)(row_ptr[v + 1] - row_ptr[v]));
+}
+
+__global__ void k_build_adjw_lists(const int32_t *__restrict__ row_ptr,
+                                   const int32_t *__restrict__ col, int32_t n, int64_t m,
+                                   uint2 *__restrict__ adj2) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    int32_t lo = 0, hi = n - 1;  // last v with row_ptr[v] <= e
+    while (lo < hi) {
+      const int32_t mid = lo + (hi - lo + 1) / 2;
+      if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int32_t y = col[e];
+    adj2[(int64_t)lo + 1 + e] =
+        make_uint2((uint32_t)(y + row_ptr[y]), (uint32_t)(row_ptr[y + 1] - row_ptr[y]));
+  }
+}
+
 __global__ void k_active_flags(const int32_t *__restrict__ row_ptr, int32_t n,
                                int32_t *__restrict__ flag) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -269,8 +294,10 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
   if ((int64_t)n + m > INT32_MAX)
     return fail(SRK_EINVAL, "n + m = %lld must stay below 2^31", (long long)n + (long long)m);
   if (!row_ptr || (m > 0 && !col)) return fail(SRK_EINVAL, "null CSR array");
-  if (flags & ~(SRK_DEVICE_PTRS | SRK_VALIDATE))
+  if (flags & ~(SRK_DEVICE_PTRS | SRK_VALIDATE | SRK_ADJ_NARROW | SRK_ADJ_WIDE))
     return fail(SRK_EINVAL, "unknown flags 0x%x", flags);
+  if ((flags & SRK_ADJ_NARROW) && (flags & SRK_ADJ_WIDE))
+    return fail(SRK_EINVAL, "SRK_ADJ_NARROW and SRK_ADJ_WIDE exclude each other");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "srk_graph_load: no CUDA device");
@@ -339,14 +366,27 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
     int pb = 1;
     while (pb < 31 && ((int64_t)1 << pb) < (int64_t)n + m) ++pb;  // positions < n + m
     g->pos_bits = pb;
-    if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) * ((size_t)n + (size_t)m))) != cudaSuccess) {
+    // 32-bit entries while their degree code reaches 31 (positions of at most
+    // 27 bits): the headers of the larger nodes are then few and stay cached,
+    // and the smaller footprint keeps more of the graph in L2.  Beyond that a
+    // code of 15 or less sends most steps to a second, uncached read, and
+    // 64-bit entries (no header read at all) are faster despite their size.
+    g->wide = (flags & SRK_ADJ_WIDE) ? 1 : (flags & SRK_ADJ_NARROW) ? 0 : (pb > 27 ? 1 : 0);
+    const size_t words = ((size_t)n + (size_t)m) * (g->wide ? 2 : 1);
+    if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) * words)) != cudaSuccess) {
       int rc = cuda_fail(e, "srk_graph_load: packed adjacency");
       srk_graph_free(g);
       return rc;
     }
-    k_build_adj_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, g->adj);
-    if (m > 0)
-      k_build_adj_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, pb, g->adj);
+    if (g->wide) {
+      uint2 *adj2 = reinterpret_cast<uint2 *>(g->adj);
+      k_build_adjw_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, adj2);
+      if (m > 0) k_build_adjw_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, adj2);
+    } else {
+      k_build_adj_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, g->adj);
+      if (m > 0)
+        k_build_adj_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, pb, g->adj);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {

@@ -31,6 +31,7 @@ namespace srk {
 // no in-neighbours.  Walks run on the packed adjacency (degree, then the
 // in-neighbours' positions), so nodes are identified by their position.  The same thread computes Fisher-Yates draw t = r,
 // k_t = floor(R * (t+1) / 2^64) with R from counter (t>>1, ~0, ~0, s).
+template <bool kWide>
 __global__ void __launch_bounds__(256)
 k_source_walks(const int32_t *__restrict__ row_ptr,
                const uint32_t *__restrict__ adj, int pos_bits,
@@ -45,8 +46,8 @@ k_source_walks(const int32_t *__restrict__ row_ptr,
   const int Ls = tab.L > 0 ? tab.L : 1;
   const uint32_t s = (uint32_t)tab.s;
   const int32_t p_s = tab.s + row_ptr[tab.s];  // position of s in adj
-  const Adj G = make_adj(adj, pos_bits);
-  const uint32_t deg_s = adj[p_s];
+  const auto G = adj_view<kWide>(adj, pos_bits);
+  const uint32_t deg_s = header_deg(G, p_s);
   unsigned long long steps = 0;
   for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < tab.N_tot;
        r += gridDim.x * blockDim.x) {
@@ -299,7 +300,7 @@ struct LiteralArgs {
 // 8 blocks of 256 threads per SM (32 registers): the kernel is bound by the
 // rate of scattered L1 misses, and full occupancy keeps the most misses in
 // flight.  kLiteral: the literal target shuffle (walk_target_literal).
-template <bool kLiteral>
+template <bool kLiteral, bool kWide>
 __global__ void __launch_bounds__(256, 8)
 k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ LiteralArgs X) {
   __shared__ int32_t cnt[SRK_MAX_LEN + 3];
@@ -317,7 +318,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const Adj G = make_adj(A.adj, A.pos_bits);
+  const auto G = adj_view<kWide>(A.adj, A.pos_bits);
   PairSet S;
   S.cnt = cnt;
   S.R = R;
@@ -345,7 +346,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
     const int32_t beg_u = u + A.row_ptr[u];  // position of u
-    const uint32_t deg_u = G.adj[beg_u];
+    const uint32_t deg_u = header_deg(G, beg_u);
     if (u != A.s && deg_u > 0) {
       if (kLiteral)
         walk_target_literal(rk, G, S, fs, Psh, A.L, X.a, (uint32_t)u, beg_u, deg_u,
@@ -413,7 +414,7 @@ static int target_grid(int device) {
   static int blocks_per_sm[64] = {};
   int b = (device >= 0 && device < 64) ? blocks_per_sm[device] : 0;
   if (!b) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks<false>, 256, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks<false, false>, 256, 0) !=
             cudaSuccess || b < 1)
       b = 1;
     if (device >= 0 && device < 64) blocks_per_sm[device] = b;
@@ -431,8 +432,12 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   const int gN = grid_for(N, 256, dev);
   cudaError_t e = cudaMemsetAsync(w.small, 0, kSmallBytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "clearing query counters");
-  k_source_walks<<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos, w.seff,
-                                     w.kdraw, w.grp_cnt, w.small);
+  if (g->wide)
+    k_source_walks<true><<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos,
+                                             w.seff, w.kdraw, w.grp_cnt, w.small);
+  else
+    k_source_walks<false><<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos,
+                                              w.seff, w.kdraw, w.grp_cnt, w.small);
   k_fy_rank<<<gN, 256, 0, st>>>(w.kdraw, w.grp_cnt, w.rank, N);
   k_scan<<<1, 1024, 0, st>>>(w.grp_cnt, w.grp_off, N);
   k_fy_scatter<<<gN, 256, 0, st>>>(w.kdraw, w.grp_off, w.rank, w.items, N);
@@ -483,10 +488,15 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
     memset(&X, 0, sizeof X);
   }
   if (timing) cudaEventRecord(timing[0], st);
-  if (t.literal)
-    k_target_walks<true><<<target_grid(dev), 256, 0, st>>>(A, X);
+  const int tg = target_grid(dev);
+  if (t.literal && g->wide)
+    k_target_walks<true, true><<<tg, 256, 0, st>>>(A, X);
+  else if (t.literal)
+    k_target_walks<true, false><<<tg, 256, 0, st>>>(A, X);
+  else if (g->wide)
+    k_target_walks<false, true><<<tg, 256, 0, st>>>(A, X);
   else
-    k_target_walks<false><<<target_grid(dev), 256, 0, st>>>(A, X);
+    k_target_walks<false, false><<<tg, 256, 0, st>>>(A, X);
   if (timing) cudaEventRecord(timing[1], st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

@@ -47,6 +47,20 @@ def test_last_error_starts_empty(lib):
     assert lib.srk_last_error() in (b"",)
 
 
+def test_graph_load_refuses_both_layouts(lib):
+    import numpy as np
+    import paper_2304_04015_gb300 as srk
+    rp = np.array([0, 1], dtype=np.int32)
+    col = np.array([0], dtype=np.int32)
+    out = ctypes.c_void_p()
+    flags = srk.SRK_ADJ_NARROW | srk.SRK_ADJ_WIDE
+    assert lib.srk_graph_load(rp.ctypes.data_as(ctypes.c_void_p),
+                              col.ctypes.data_as(ctypes.c_void_p), 1, 1, flags, None,
+                              ctypes.byref(out)) == srk.SRK_EINVAL
+    lib.srk_last_error.restype = ctypes.c_char_p
+    assert b"exclude each other" in lib.srk_last_error()
+
+
 def test_graph_load_rejects_bad_arguments_without_touching_the_device(lib):
     # argument checks run before any CUDA call
     import paper_2304_04015_gb300 as srk

@@ -435,3 +435,50 @@ def test_gather_probe_cache_operators(srk):
     with pytest.raises(srk.SrkError) as e:
         srk.srk_probe_gather_ex(data, 8, 3, 7, sink)
     assert e.value.code == srk.SRK_EINVAL
+
+
+def test_wide_adjacency_layout_bit_exact(srk):
+    # the 8-byte-entry layout (forced here on small graphs) gives exactly the
+    # results of the 4-byte one: single-source, literal shuffle and batched
+    import torch
+    dev = torch.device("cuda:0")
+    cases = [(er_graph(1000, 5.0, 1), 0, 0.1, TINY), (rmat_graph(16), 4242, 0.05, {})]
+    for (rp, col), s, eps, kw in cases:
+        n = rp.size - 1
+        outs = []
+        for layout in ("narrow", "wide"):
+            g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                                   layout=layout)
+            try:
+                sc = torch.empty(n, dtype=torch.float64, device=dev)
+                cn = torch.empty(n, dtype=torch.int32, device=dev)
+                stp = torch.empty(n, dtype=torch.int32, device=dev)
+                st = srk.SrkStats()
+                srk.srk_single_source(g, s, C, eps, 7, sc, cn, step_counts=stp, stats=st, **kw)
+                lit = torch.empty(n, dtype=torch.int32, device=dev)
+                srk.srk_single_source(g, s, C, eps, 7, torch.empty(n, dtype=torch.float64,
+                                                                    device=dev), lit,
+                                      literal_shuffle=True, **kw)
+                multi = torch.empty((2, n), dtype=torch.float64, device=dev)
+                srk.srk_multi_source(g, [s, 3], C, [eps, eps], 7, multi, **kw)
+                torch.cuda.synchronize()
+                outs.append((sc.cpu().numpy(), cn.cpu().numpy(), stp.cpu().numpy(),
+                             lit.cpu().numpy(), multi.cpu().numpy(), st.source_steps,
+                             st.target_steps))
+            finally:
+                g.close()
+        for a, b in zip(outs[0], outs[1]):
+            assert np.array_equal(a, b)
+        assert outs[1][1].sum() > 0
+    # and the wide layout against the oracle directly
+    rp, col = er_graph(1000, 5.0, 1)
+    g = srk.srk_graph_load(rp, col, layout="wide")
+    try:
+        n = rp.size - 1
+        counts = np.empty(n, dtype=np.uint32)
+        scores = np.empty(n)
+        srk.srk_single_source(g, 17, C, 0.1, 2, scores, counts, **TINY)
+    finally:
+        g.close()
+    ref = oracle_query(rp, col, 17, 0.1, 2, **TINY)
+    assert np.array_equal(counts, ref.count) and np.array_equal(scores, ref.scores)
