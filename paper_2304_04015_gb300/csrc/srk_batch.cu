@@ -381,12 +381,12 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
   if (!sources || !eps || !scores) return fail(SRK_EINVAL, "null argument");
   if (opt && opt->step_counts)
     return fail(SRK_EINVAL, "step_counts is not supported by srk_multi_source");
+  if (opt && (opt->flags & SRK_OPT_LITERAL_SHUFFLE))
+    return fail(SRK_EINVAL, "the literal shuffle is not supported by srk_multi_source");
   if (opt && (opt->flags & ~(SRK_OPT_NO_GRAPH | SRK_OPT_WARMUP_RULE)))
     return fail(SRK_EINVAL, "unknown opts.flags 0x%x", opt->flags);
   if (opt && (opt->target_begin != 0 || opt->target_end != 0))
     return fail(SRK_EINVAL, "target ranges are not supported by srk_multi_source");
-  if (opt && (opt->flags & SRK_OPT_LITERAL_SHUFFLE))
-    return fail(SRK_EINVAL, "the literal shuffle is not supported by srk_multi_source");
   const bool use_graph = !(opt && (opt->flags & SRK_OPT_NO_GRAPH));
   const size_t n = (size_t)g->n;
   // a1 for every source (host, FP64)

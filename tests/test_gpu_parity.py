@@ -482,3 +482,39 @@ def test_wide_adjacency_layout_bit_exact(srk):
         g.close()
     ref = oracle_query(rp, col, 17, 0.1, 2, **TINY)
     assert np.array_equal(counts, ref.count) and np.array_equal(scores, ref.scores)
+
+
+def test_degenerate_graphs_and_calls(srk):
+    import torch
+    dev = torch.device("cuda:0")
+    # one node, no edges: s~(0, 0) = 1, single and batched
+    g = srk.srk_graph_load(np.array([0, 0], dtype=np.int32), np.zeros(0, dtype=np.int32))
+    try:
+        sc = torch.full((1,), -1.0, dtype=torch.float64, device=dev)
+        srk.srk_single_source(g, 0, C, 0.9, 1, sc, z_override=10.0)
+        multi = torch.full((2, 1), -1.0, dtype=torch.float64, device=dev)
+        srk.srk_multi_source(g, [0, 0], C, [0.9, 0.9], 1, multi, z_override=10.0)
+        torch.cuda.synchronize()
+        assert sc.item() == 1.0 and bool(torch.all(multi == 1.0))
+        srk.srk_multi_source(g, [], C, [], 1, multi)       # no sources: nothing to do
+    finally:
+        g.close()
+    # self-loops and repeated in-neighbours are valid CSR input: a walk may
+    # stay on a node and a repeated neighbour is drawn twice as often
+    lists = [[0, 1, 1], [0, 2], [2, 2, 3], [1], [], [0, 4, 4, 5], [5]]
+    rp = np.zeros(len(lists) + 1, dtype=np.int32)
+    rp[1:] = np.cumsum([len(x) for x in lists])
+    col = np.array([y for x in lists for y in x], dtype=np.int32)
+    for s in (0, 2, 5):
+        gpu = gpu_query(srk, rp, col, s, 0.5, 3, z_override=400.0, L_override=12)
+        ref = oracle_query(rp, col, s, 0.5, 3, z_override=400.0, L_override=12)
+        assert_parity(gpu, ref)
+        assert gpu[1].sum() > 0
+    # an empty target range leaves the outputs untouched
+    g = srk.srk_graph_load(rp, col)
+    try:
+        out = np.full(rp.size - 1, -5.0)
+        srk.srk_single_source(g, 0, C, 0.5, 3, out, z_override=100.0, target_range=(3, 3))
+        assert np.all(out == -5.0)
+    finally:
+        g.close()
