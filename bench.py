@@ -65,7 +65,7 @@ def parse():
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
-    ap.add_argument("--layout", default=None, choices=["narrow", "wide"],
+    ap.add_argument("--layout", default=None, choices=["narrow", "wide", "csr"],
                     help="adjacency entry layout (default: chosen by graph size)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -198,6 +198,16 @@ def gather_probe(srk, torch, dev, n_words, cache_ops=(0,)):
         rates.append(rate)
     del data
     return rates
+
+
+def adjacency_layout(n, m, forced):
+    """The adjacency layout srk_graph_load picks (or the forced one)."""
+    if forced:
+        return forced
+    pb = 1
+    while pb < 31 and (1 << pb) < n + m:
+        pb += 1
+    return "narrow" if pb <= 26 else ("csr" if pb == 27 else "wide")
 
 
 def kernel_source_sha256():
@@ -352,7 +362,7 @@ def run_batch(args, rank, world):
             "source_in_degrees": [int(deg[s]) for s in sources], "eps": eps,
             "target_steps": st.target_steps, "walk_steps_per_s": st.target_steps / t_batch,
             "batch_shape": st.batch_shape, "graph_gen_s": t_gen,
-            "adjacency": args.layout or ("wide" if n + m > (1 << 27) else "narrow"),
+            "adjacency": adjacency_layout(n, m, args.layout),
             "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
     print(json.dumps(line), flush=True)
@@ -760,7 +770,7 @@ def main():
                        "(0.57,0.19,0.19,0.05), dedup, no self-loops, seed %d" % GRAPH_SEED,
                        "n": n, "m": m, "c": C, "eps": EPS, "sources": N_SOURCES,
                        "source_seed": SOURCE_SEED, "query_seed": QUERY_SEED,
-                       "adjacency": args.layout or ("wide" if n + m > (1 << 27) else "narrow"),
+                       "adjacency": adjacency_layout(n, m, args.layout),
                        "z": stats_steps[0][4], "N_tot": stats_steps[0][2],
                        "L": int(np.floor(np.log(n) / -np.log(np.sqrt(C)))),
                        "l2": "256 MB buffer written between queries (outside the timed intervals)",

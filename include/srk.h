@@ -73,6 +73,7 @@ extern "C" {
 #define SRK_VALIDATE    2  /* accepted; the CSR invariants are always checked */
 #define SRK_ADJ_NARROW  4  /* force 4-byte adjacency entries (see srk_graph_load) */
 #define SRK_ADJ_WIDE    8  /* force 8-byte adjacency entries (see srk_graph_load) */
+#define SRK_ADJ_CSR    16  /* walks read row_ptr and col directly (see srk_graph_load) */
 
 /* Upper bounds of this build. */
 #define SRK_MAX_LEN   255          /* largest truncation length L */
@@ -124,14 +125,15 @@ typedef struct srk_opts {
  *                  are borrowed; the caller keeps them alive and unchanged
  *                  until srk_graph_free.  Otherwise they are host arrays and
  *                  are copied.  SRK_VALIDATE is accepted and implied.
- *                  SRK_ADJ_NARROW / SRK_ADJ_WIDE force the layout of the
- *                  packed adjacency the walks read (4-byte entries carrying a
- *                  degree code of 32 - ceil(log2(n + m)) bits, or 8-byte
- *                  entries carrying the full degree); by default 4-byte
- *                  entries are used while n + m <= 2^27 and 8-byte entries
- *                  beyond, where a narrow code (15 or less) would send most
- *                  steps to a second random read.  Results do not depend on
- *                  the layout; giving both flags is SRK_EINVAL.
+ *                  SRK_ADJ_NARROW / SRK_ADJ_WIDE / SRK_ADJ_CSR force the
+ *                  adjacency layout the walks read: a packed copy with
+ *                  4-byte entries carrying a degree code of
+ *                  32 - ceil(log2(n + m)) bits, a packed copy with 8-byte
+ *                  entries carrying the full degree, or row_ptr and col
+ *                  themselves (no copy).  By default: 4-byte entries while
+ *                  n + m <= 2^26, the CSR while n + m <= 2^27, 8-byte
+ *                  entries beyond.  Results do not depend on the layout;
+ *                  giving more than one of the flags is SRK_EINVAL.
  * The CSR invariants (row_ptr[0] = 0, row_ptr[n] = m, row_ptr non-decreasing,
  * 0 <= col < n) are always checked on the device before the handle is
  * returned; a violation returns SRK_EINVAL.  The walk kernels rely on them.

@@ -35,7 +35,7 @@ __all__ = [
 ]
 
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
-SRK_DEVICE_PTRS, SRK_VALIDATE, SRK_ADJ_NARROW, SRK_ADJ_WIDE = 1, 2, 4, 8
+SRK_DEVICE_PTRS, SRK_VALIDATE, SRK_ADJ_NARROW, SRK_ADJ_WIDE, SRK_ADJ_CSR = 1, 2, 4, 8, 16
 SRK_OPT_NO_GRAPH, SRK_OPT_WARMUP_RULE, SRK_OPT_LITERAL_SHUFFLE = 1, 2, 4
 SRK_PROBE_DEFAULT, SRK_PROBE_CG, SRK_PROBE_NC, SRK_PROBE_CA = 0, 1, 2, 3
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
@@ -215,7 +215,7 @@ def srk_graph_load(row_ptr, col, n: Optional[int] = None, m: Optional[int] = Non
     if flags is None:
         flags = SRK_DEVICE_PTRS if rp_dev else 0
     if layout is not None:
-        flags |= {"narrow": SRK_ADJ_NARROW, "wide": SRK_ADJ_WIDE}[layout]
+        flags |= {"narrow": SRK_ADJ_NARROW, "wide": SRK_ADJ_WIDE, "csr": SRK_ADJ_CSR}[layout]
     if rp_dev != cl_dev or (edge_w is not None and ew_dev != rp_dev):
         raise ValueError("row_ptr, col and edge_w must all be on the device or all on the host")
     h = _vp()

@@ -44,6 +44,7 @@ struct BatchArgs {
   int32_t k;
   int64_t total_walks;
   const int32_t *row_ptr;
+  const int32_t *col;
   const uint32_t *adj;
   int32_t pos_bits;
   uint32_t key0, key1;
@@ -68,14 +69,14 @@ __device__ __forceinline__ int find_source(const int64_t *off, int k, int64_t g)
   }
 
 // a2: source walks and Fisher-Yates draws of every source of the batch.
-template <bool kWide>
+template <int kLayout>
 __global__ void __launch_bounds__(256) kb_source_walks(const __grid_constant__ BatchArgs A) {
   const RoundKeys rk = round_keys(A.key0, A.key1);
-  const auto G = adj_view<kWide>(A.adj, A.pos_bits);
+  const auto G = adj_view<kLayout>(A.adj, A.pos_bits, A.row_ptr, A.col);
   SRK_BATCH_LOOP(A, {
     const QueryTab &t = *S_.tab;
     const uint32_t s = (uint32_t)S_.s;
-    const int32_t p_s = S_.s + A.row_ptr[S_.s];
+    const int32_t p_s = node_pos(G, A.row_ptr, S_.s);
     const int Ls = S_.L > 0 ? S_.L : 1;
     S_.w.grp_cnt[r_] = 0;
     S_.w.kdraw[r_] = (r_ >= 1) ? fy_draw(rk, s, r_) : 0;
@@ -239,7 +240,7 @@ __global__ void kb_prefill(const BatchSrc *__restrict__ src, int32_t k, int32_t 
 // list pointers and the rows cnt[0..L+2], R[0..L+2] (dynamic shared memory,
 // 2 (Lmax + 3) words per warp), so the walk loop holds no per-source state
 // in registers.
-template <int kBlock, int kMinBlocks, bool kWide>
+template <int kBlock, int kMinBlocks, int kLayout>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
                 int32_t n_act, const int32_t *__restrict__ act_src,
@@ -251,7 +252,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const auto G = adj_view<kWide>(A.adj, A.pos_bits);
+  const auto G = adj_view<kLayout>(A.adj, A.pos_bits, A.row_ptr, A.col);
   int32_t *my_cnt = rows + (2 * wib) * row_words;
   int32_t *my_R = my_cnt + row_words;
   const int64_t n_items = (int64_t)(*n_act_src_p) * n_act;
@@ -292,7 +293,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     if (u == A.src[i].s) continue;  // prefilled with 1
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
-    const int32_t beg_u = u + A.row_ptr[u];
+    const int32_t beg_u = node_pos(G, A.row_ptr, u);
     walk_target(rk, G, ctx[wib], (uint32_t)u, beg_u, header_deg(G, beg_u), lanes_below, c, W,
                 st);
     for (int off = 16; off > 0; off >>= 1) {
@@ -317,21 +318,21 @@ struct Shape {
 static const Shape kShapes[] = {{256, 8}, {512, 4}, {128, 16}, {1024, 2}, {256, 6}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <bool kWide>
+template <int kLayout>
 static void launch_targets_t(int shape, int grid, int block, size_t smem, cudaStream_t st,
                              const BatchArgs &A, const int32_t *act, int32_t n_act,
                              const int32_t *act_src, const int32_t *n_act_src,
                              unsigned long long *ctr, int64_t limit, int32_t rw) {
   switch (shape) {
-    case 0: kb_target_walks<256, 8, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 1: kb_target_walks<512, 4, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 2: kb_target_walks<128, 16, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 3: kb_target_walks<1024, 2, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    default: kb_target_walks<256, 6, kWide><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 0: kb_target_walks<256, 8, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 1: kb_target_walks<512, 4, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 2: kb_target_walks<128, 16, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 3: kb_target_walks<1024, 2, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    default: kb_target_walks<256, 6, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
   }
 }
 
-static void launch_targets(bool wide, int shape, int sms, cudaStream_t st, const BatchArgs &A,
+static void launch_targets(int layout, int shape, int sms, cudaStream_t st, const BatchArgs &A,
                            const int32_t *act, int32_t n_act, const int32_t *act_src,
                            const int32_t *n_act_src, unsigned long long *ctr,
                            int64_t limit, int Lmax) {
@@ -339,12 +340,15 @@ static void launch_targets(bool wide, int shape, int sms, cudaStream_t st, const
   const int grid = sms * sh.per_sm;
   const int32_t rw = Lmax + 3;
   const size_t smem = sizeof(int32_t) * 2 * (size_t)rw * (size_t)(sh.block / 32);
-  if (wide)
-    launch_targets_t<true>(shape, grid, sh.block, smem, st, A, act, n_act, act_src, n_act_src,
+  if (layout == kWide)
+    launch_targets_t<kWide>(shape, grid, sh.block, smem, st, A, act, n_act, act_src,
+                            n_act_src, ctr, limit, rw);
+  else if (layout == kCsr)
+    launch_targets_t<kCsr>(shape, grid, sh.block, smem, st, A, act, n_act, act_src, n_act_src,
                            ctr, limit, rw);
   else
-    launch_targets_t<false>(shape, grid, sh.block, smem, st, A, act, n_act, act_src,
-                            n_act_src, ctr, limit, rw);
+    launch_targets_t<kNarrow>(shape, grid, sh.block, smem, st, A, act, n_act, act_src,
+                              n_act_src, ctr, limit, rw);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -493,6 +497,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     A.k = kb;
     A.total_walks = hoff[(size_t)kb];
     A.row_ptr = g->row_ptr;
+    A.col = g->col;
     A.adj = g->adj;
     A.pos_bits = g->pos_bits;
     A.key0 = (uint32_t)seed;
@@ -503,10 +508,12 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       for (int32_t b = 0; b < kb; ++b)
         cudaMemsetAsync(hsrc[(size_t)b].w.small, 0, kSmallBytes, s2);
       cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * (kb + 1), s2);
-      if (g->wide)
-        kb_source_walks<true><<<gw, 256, 0, s2>>>(A);
+      if (g->layout == kWide)
+        kb_source_walks<kWide><<<gw, 256, 0, s2>>>(A);
+      else if (g->layout == kCsr)
+        kb_source_walks<kCsr><<<gw, 256, 0, s2>>>(A);
       else
-        kb_source_walks<false><<<gw, 256, 0, s2>>>(A);
+        kb_source_walks<kNarrow><<<gw, 256, 0, s2>>>(A);
       kb_fy_rank<<<gw, 256, 0, s2>>>(A);
       kb_scan<<<kb, 1024, 0, s2>>>(A);
       kb_fy_scatter<<<gw, 256, 0, s2>>>(A);
@@ -531,7 +538,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       for (int sh = 0; sh < kNumShapes; ++sh) {
         cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
         cudaEventRecord(t0, st);
-        launch_targets(g->wide, sh, sms, st, A, g->act, g->n_act, d_act_src, d_act_src + kb,
+        launch_targets(g->layout, sh, sms, st, A, g->act, g->n_act, d_act_src, d_act_src + kb,
                        d_ctr, trial, Lmax);
         cudaEventRecord(t1, st);
         float ms = 0.f;
@@ -547,7 +554,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     }
     auto enqueue_all = [&](cudaStream_t s2) {
       enqueue_source_side(s2);
-      launch_targets(g->wide, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
+      launch_targets(g->layout, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
                      d_ctr, INT64_MAX, Lmax);
     };
     if (use_graph) {

@@ -164,10 +164,43 @@ __device__ __forceinline__ int32_t entry_pos(const AdjW &, uint2 e) { return (in
 __device__ __forceinline__ uint32_t entry_deg(const AdjW &, uint2 e, int32_t) { return e.y; }
 __device__ __forceinline__ uint32_t header_deg(const AdjW &G, int32_t p) { return G.adj[p].y; }
 
-// The view of a graph's adjacency words in the layout kWide names.
-template <bool kWide>
-__device__ __forceinline__ auto adj_view(const uint32_t *words, int pb) {
-  if constexpr (kWide) return make_adjw(words);
+// The CSR layout: nodes are their own ids, a step reads row_ptr[x] and
+// row_ptr[x+1] (the list and its degree) and one col entry.
+struct AdjC {
+  const int32_t *row_ptr;
+  const int32_t *col;
+};
+__device__ __forceinline__ uint32_t header_deg(const AdjC &G, int32_t v) {
+  return (uint32_t)(G.row_ptr[v + 1] - G.row_ptr[v]);
+}
+__device__ __forceinline__ int32_t adj_entry(const AdjC &G, int32_t v, uint32_t deg,
+                                             uint32_t hi, uint32_t lo) {
+  return G.col[G.row_ptr[v] + (int32_t)draw_index(hi, lo, deg)];
+}
+__device__ __forceinline__ int32_t entry_pos(const AdjC &, int32_t e) { return e; }
+__device__ __forceinline__ uint32_t entry_deg(const AdjC &G, int32_t, int32_t x) {
+  return header_deg(G, x);
+}
+
+// The identity of node v inside the walk kernels: its position in the
+// packed layouts, its id in the CSR layout.
+__device__ __forceinline__ int32_t node_pos(const Adj &, const int32_t *row_ptr, int32_t v) {
+  return v + row_ptr[v];
+}
+__device__ __forceinline__ int32_t node_pos(const AdjW &, const int32_t *row_ptr, int32_t v) {
+  return v + row_ptr[v];
+}
+__device__ __forceinline__ int32_t node_pos(const AdjC &, const int32_t *, int32_t v) { return v; }
+
+// Adjacency layouts (srk_graph::layout).
+constexpr int kNarrow = 0, kWide = 1, kCsr = 2;
+
+// The view of a graph's adjacency in layout kLayout.
+template <int kLayout>
+__device__ __forceinline__ auto adj_view(const uint32_t *words, int pb, const int32_t *row_ptr,
+                                         const int32_t *col) {
+  if constexpr (kLayout == kWide) return make_adjw(words);
+  else if constexpr (kLayout == kCsr) return AdjC{row_ptr, col};
   else return make_adj(words, pb);
 }
 

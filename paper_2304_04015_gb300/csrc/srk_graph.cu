@@ -294,10 +294,14 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
   if ((int64_t)n + m > INT32_MAX)
     return fail(SRK_EINVAL, "n + m = %lld must stay below 2^31", (long long)n + (long long)m);
   if (!row_ptr || (m > 0 && !col)) return fail(SRK_EINVAL, "null CSR array");
-  if (flags & ~(SRK_DEVICE_PTRS | SRK_VALIDATE | SRK_ADJ_NARROW | SRK_ADJ_WIDE))
+  if (flags & ~(SRK_DEVICE_PTRS | SRK_VALIDATE | SRK_ADJ_NARROW | SRK_ADJ_WIDE | SRK_ADJ_CSR))
     return fail(SRK_EINVAL, "unknown flags 0x%x", flags);
-  if ((flags & SRK_ADJ_NARROW) && (flags & SRK_ADJ_WIDE))
-    return fail(SRK_EINVAL, "SRK_ADJ_NARROW and SRK_ADJ_WIDE exclude each other");
+  {
+    const int layouts = !!(flags & SRK_ADJ_NARROW) + !!(flags & SRK_ADJ_WIDE) +
+                        !!(flags & SRK_ADJ_CSR);
+    if (layouts > 1)
+      return fail(SRK_EINVAL, "SRK_ADJ_NARROW, SRK_ADJ_WIDE and SRK_ADJ_CSR exclude each other");
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "srk_graph_load: no CUDA device");
@@ -366,19 +370,27 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
     int pb = 1;
     while (pb < 31 && ((int64_t)1 << pb) < (int64_t)n + m) ++pb;  // positions < n + m
     g->pos_bits = pb;
-    // 32-bit entries while their degree code reaches 31 (positions of at most
-    // 27 bits): the headers of the larger nodes are then few and stay cached,
-    // and the smaller footprint keeps more of the graph in L2.  Beyond that a
-    // code of 15 or less sends most steps to a second, uncached read, and
-    // 64-bit entries (no header read at all) are faster despite their size.
-    g->wide = (flags & SRK_ADJ_WIDE) ? 1 : (flags & SRK_ADJ_NARROW) ? 0 : (pb > 27 ? 1 : 0);
-    const size_t words = ((size_t)n + (size_t)m) * (g->wide ? 2 : 1);
+    // Layout by size (measured on R-MAT graphs): 32-bit entries while their
+    // degree code reaches 63 (positions of at most 26 bits; the headers read
+    // for larger nodes are few and cached, and the graph or most of it stays
+    // in L2); at 27 bits the plain CSR (row_ptr, 4 B per node, stays in L2
+    // while the col reads go to DRAM); beyond, 64-bit entries: a code of 15
+    // or less would send most steps to a second, uncached read.
+    g->layout = (flags & SRK_ADJ_WIDE)     ? 1
+                : (flags & SRK_ADJ_CSR)    ? 2
+                : (flags & SRK_ADJ_NARROW) ? 0
+                : pb <= 26                 ? 0
+                : pb == 27                 ? 2
+                                           : 1;
+    const size_t words = g->layout == 2 ? 1 : ((size_t)n + (size_t)m) * (g->layout == 1 ? 2 : 1);
     if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) * words)) != cudaSuccess) {
       int rc = cuda_fail(e, "srk_graph_load: packed adjacency");
       srk_graph_free(g);
       return rc;
     }
-    if (g->wide) {
+    if (g->layout == 2) {
+      // the walks read row_ptr and col directly
+    } else if (g->layout == 1) {
       uint2 *adj2 = reinterpret_cast<uint2 *>(g->adj);
       k_build_adjw_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, adj2);
       if (m > 0) k_build_adjw_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, adj2);

@@ -19,13 +19,15 @@ struct srk_graph {
   // so a walk step learns the next node's degree from the entry it reads and
   // reads the header only when the degree is deg_max or more.  A node's
   // position is its identity inside the walk kernels.
-  // Wide layout (wide = 1, chosen when positions need more than 27 bits or
-  // forced by SRK_ADJ_WIDE): 2 (n + m) words forming 8-byte entries at the
-  // same positions, adj[pos(v)] = {0, |I(v)|} and entries {pos(y), |I(y)|},
-  // so a step never reads a header.
+  // Wide layout (layout = 1, chosen when positions need more than 27 bits
+  // or forced by SRK_ADJ_WIDE): 2 (n + m) words forming 8-byte entries at
+  // the same positions, adj[pos(v)] = {0, |I(v)|} and entries
+  // {pos(y), |I(y)|}, so a step never reads a header.  CSR layout (layout =
+  // 2, at 27 bits or forced by SRK_ADJ_CSR): no packed copy; nodes are their
+  // ids and a step reads row_ptr and col.
   uint32_t *adj = nullptr;
   int32_t pos_bits = 1;  // positions < 2^pos_bits
-  int wide = 0;
+  int layout = 0;        // 0 narrow, 1 wide, 2 CSR (no packed adjacency; walks read row_ptr/col)
   // Nodes with at least one in-neighbour, ascending (owned): the only targets
   // whose score can be nonzero.
   int32_t *act = nullptr;

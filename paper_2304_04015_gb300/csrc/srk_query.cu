@@ -31,9 +31,9 @@ namespace srk {
 // no in-neighbours.  Walks run on the packed adjacency (degree, then the
 // in-neighbours' positions), so nodes are identified by their position.  The same thread computes Fisher-Yates draw t = r,
 // k_t = floor(R * (t+1) / 2^64) with R from counter (t>>1, ~0, ~0, s).
-template <bool kWide>
+template <int kLayout>
 __global__ void __launch_bounds__(256)
-k_source_walks(const int32_t *__restrict__ row_ptr,
+k_source_walks(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                const uint32_t *__restrict__ adj, int pos_bits,
                const __grid_constant__ QueryTab tab,
                int32_t *__restrict__ spos, int32_t *__restrict__ seff,
@@ -45,8 +45,8 @@ k_source_walks(const int32_t *__restrict__ row_ptr,
   const RoundKeys rk = round_keys(tab.key0, tab.key1);
   const int Ls = tab.L > 0 ? tab.L : 1;
   const uint32_t s = (uint32_t)tab.s;
-  const int32_t p_s = tab.s + row_ptr[tab.s];  // position of s in adj
-  const auto G = adj_view<kWide>(adj, pos_bits);
+  const auto G = adj_view<kLayout>(adj, pos_bits, row_ptr, col);
+  const int32_t p_s = node_pos(G, row_ptr, tab.s);  // s inside the kernels
   const uint32_t deg_s = header_deg(G, p_s);
   unsigned long long steps = 0;
   for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < tab.N_tot;
@@ -271,6 +271,7 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
 // (s~(s,s) = 1).
 struct TargetArgs {
   const int32_t *row_ptr;  // start positions of the targets: u + row_ptr[u]
+  const int32_t *col;      // in-neighbour lists (CSR layout)
   const uint32_t *adj;     // packed adjacency (see srk_internal.h)
   int32_t pos_bits;
   int32_t n, s, L;
@@ -300,7 +301,7 @@ struct LiteralArgs {
 // 8 blocks of 256 threads per SM (32 registers): the kernel is bound by the
 // rate of scattered L1 misses, and full occupancy keeps the most misses in
 // flight.  kLiteral: the literal target shuffle (walk_target_literal).
-template <bool kLiteral, bool kWide>
+template <bool kLiteral, int kLayout>
 __global__ void __launch_bounds__(256, 8)
 k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ LiteralArgs X) {
   __shared__ int32_t cnt[SRK_MAX_LEN + 3];
@@ -318,7 +319,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const auto G = adj_view<kWide>(A.adj, A.pos_bits);
+  const auto G = adj_view<kLayout>(A.adj, A.pos_bits, A.row_ptr, A.col);
   PairSet S;
   S.cnt = cnt;
   S.R = R;
@@ -345,7 +346,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
     if (u < 0) break;
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
-    const int32_t beg_u = u + A.row_ptr[u];  // position of u
+    const int32_t beg_u = node_pos(G, A.row_ptr, u);  // u inside the kernels
     const uint32_t deg_u = header_deg(G, beg_u);
     if (u != A.s && deg_u > 0) {
       if (kLiteral)
@@ -414,7 +415,7 @@ static int target_grid(int device) {
   static int blocks_per_sm[64] = {};
   int b = (device >= 0 && device < 64) ? blocks_per_sm[device] : 0;
   if (!b) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks<false, false>, 256, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_target_walks<false, kNarrow>, 256, 0) !=
             cudaSuccess || b < 1)
       b = 1;
     if (device >= 0 && device < 64) blocks_per_sm[device] = b;
@@ -432,12 +433,15 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   const int gN = grid_for(N, 256, dev);
   cudaError_t e = cudaMemsetAsync(w.small, 0, kSmallBytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "clearing query counters");
-  if (g->wide)
-    k_source_walks<true><<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos,
-                                             w.seff, w.kdraw, w.grp_cnt, w.small);
+  if (g->layout == kWide)
+    k_source_walks<kWide><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->pos_bits, t,
+                                              w.spos, w.seff, w.kdraw, w.grp_cnt, w.small);
+  else if (g->layout == kCsr)
+    k_source_walks<kCsr><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->pos_bits, t,
+                                             w.spos, w.seff, w.kdraw, w.grp_cnt, w.small);
   else
-    k_source_walks<false><<<gN, 256, 0, st>>>(g->row_ptr, g->adj, g->pos_bits, t, w.spos,
-                                              w.seff, w.kdraw, w.grp_cnt, w.small);
+    k_source_walks<kNarrow><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->pos_bits, t,
+                                                w.spos, w.seff, w.kdraw, w.grp_cnt, w.small);
   k_fy_rank<<<gN, 256, 0, st>>>(w.kdraw, w.grp_cnt, w.rank, N);
   k_scan<<<1, 1024, 0, st>>>(w.grp_cnt, w.grp_off, N);
   k_fy_scatter<<<gN, 256, 0, st>>>(w.kdraw, w.grp_off, w.rank, w.items, N);
@@ -458,6 +462,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
                                   w.pair_w, w.Hc);
   TargetArgs A;
   A.row_ptr = g->row_ptr;
+  A.col = g->col;
   A.adj = g->adj;
   A.pos_bits = g->pos_bits;
   A.n = g->n;
@@ -489,14 +494,14 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   }
   if (timing) cudaEventRecord(timing[0], st);
   const int tg = target_grid(dev);
-  if (t.literal && g->wide)
-    k_target_walks<true, true><<<tg, 256, 0, st>>>(A, X);
-  else if (t.literal)
-    k_target_walks<true, false><<<tg, 256, 0, st>>>(A, X);
-  else if (g->wide)
-    k_target_walks<false, true><<<tg, 256, 0, st>>>(A, X);
-  else
-    k_target_walks<false, false><<<tg, 256, 0, st>>>(A, X);
+  switch (g->layout * 2 + (t.literal ? 1 : 0)) {
+    case 2 * kWide: k_target_walks<false, kWide><<<tg, 256, 0, st>>>(A, X); break;
+    case 2 * kWide + 1: k_target_walks<true, kWide><<<tg, 256, 0, st>>>(A, X); break;
+    case 2 * kCsr: k_target_walks<false, kCsr><<<tg, 256, 0, st>>>(A, X); break;
+    case 2 * kCsr + 1: k_target_walks<true, kCsr><<<tg, 256, 0, st>>>(A, X); break;
+    case 2 * kNarrow + 1: k_target_walks<true, kNarrow><<<tg, 256, 0, st>>>(A, X); break;
+    default: k_target_walks<false, kNarrow><<<tg, 256, 0, st>>>(A, X); break;
+  }
   if (timing) cudaEventRecord(timing[1], st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

@@ -446,7 +446,7 @@ def test_wide_adjacency_layout_bit_exact(srk):
     for (rp, col), s, eps, kw in cases:
         n = rp.size - 1
         outs = []
-        for layout in ("narrow", "wide"):
+        for layout in ("narrow", "wide", "csr"):
             g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
                                    layout=layout)
             try:
@@ -467,8 +467,9 @@ def test_wide_adjacency_layout_bit_exact(srk):
                              st.target_steps))
             finally:
                 g.close()
-        for a, b in zip(outs[0], outs[1]):
-            assert np.array_equal(a, b)
+        for other in outs[1:]:
+            for a, b in zip(outs[0], other):
+                assert np.array_equal(a, b)
         assert outs[1][1].sum() > 0
     # and the wide layout against the oracle directly
     rp, col = er_graph(1000, 5.0, 1)
