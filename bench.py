@@ -65,6 +65,10 @@ def parse():
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--literal-shuffle", action="store_true",
+                    help="plain workload with every target's walks shuffled too")
+    ap.add_argument("--warmup-rule", action="store_true",
+                    help="plain workload with the warm-up algorithm's sample size and truncation")
     ap.add_argument("--layout", default=None, choices=["narrow", "wide", "csr"],
                     help="adjacency entry layout (default: chosen by graph size)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
@@ -200,6 +204,21 @@ def gather_probe(srk, torch, dev, n_words, cache_ops=(0,)):
     return rates
 
 
+def variant_name(args):
+    """The estimator variant of the plain workload's queries."""
+    if args.literal_shuffle and args.warmup_rule:
+        return "literal shuffle + warm-up sample rule"
+    if args.literal_shuffle:
+        return "literal shuffle (every target's walks shuffled, Section 5.2)"
+    if args.warmup_rule:
+        return "warm-up sample rule (Section 3)"
+    return "paper defaults (source walks shuffled)"
+
+
+def variant_suffix(args):
+    return ("_literal" if args.literal_shuffle else "") + ("_warmup" if args.warmup_rule else "")
+
+
 def adjacency_layout(n, m, forced):
     """The adjacency layout srk_graph_load picks (or the forced one)."""
     if forced:
@@ -234,8 +253,9 @@ def recorded_traffic():
         return None
 
 
-def cpu_baseline(rp, col, sources, budget_s):
-    """The oracle as it stands, on the host cores, on a bounded target sample."""
+def cpu_baseline(rp, col, sources, budget_s, **variant):
+    """The oracle as it stands, on the host cores, on a bounded target sample
+    (``variant``: the literal_shuffle / warmup_rule options of the queries)."""
     from oracle import sampler
     n = rp.size - 1
     s = int(sources[0])
@@ -245,7 +265,8 @@ def cpu_baseline(rp, col, sources, budget_s):
     while True:
         targets = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int32)
         t0 = time.perf_counter()
-        res = sampler.run(rp, col, n, s, C, EPS, QUERY_SEED, targets=targets, threads=threads)
+        res = sampler.run(rp, col, n, s, C, EPS, QUERY_SEED, targets=targets, threads=threads,
+                          **variant)
         dt = time.perf_counter() - t0
         if dt >= budget_s / 4 or k >= n:
             break
@@ -666,7 +687,9 @@ def main():
     def query(i, out, timing=None, stats=None):
         s = int(my_sources[i % len(my_sources)])
         srk.srk_single_source(g, s, C, EPS, QUERY_SEED, out, stats=stats,
-                              timing_events=timing, stream=stream)
+                              timing_events=timing, stream=stream,
+                              literal_shuffle=args.literal_shuffle,
+                              warmup_rule=args.warmup_rule)
 
     # warm-up
     for i in range(args.warmup):
@@ -678,7 +701,8 @@ def main():
     for i in range(args.steps):
         st = srk.SrkStats()
         query(i, scores, stats=st)
-        stats_steps.append((st.target_steps, st.source_steps, st.n_walks, st.n_active_pairs, st.z))
+        stats_steps.append((st.target_steps, st.source_steps, st.n_walks, st.n_active_pairs,
+                            st.z, st.L))
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -760,19 +784,22 @@ def main():
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(rp, col, sources, args.cpu_seconds)
+        base = cpu_baseline(rp, col, sources, args.cpu_seconds,
+                            literal_shuffle=args.literal_shuffle, warmup_rule=args.warmup_rule)
 
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph": "R-MAT scale 20, edge factor 16, "
+            "config": {"workload": WORKLOAD + variant_suffix(args),
+                       "variant": variant_name(args),
+                       "graph": "R-MAT scale 20, edge factor 16, "
                        "(0.57,0.19,0.19,0.05), dedup, no self-loops, seed %d" % GRAPH_SEED,
                        "n": n, "m": m, "c": C, "eps": EPS, "sources": N_SOURCES,
                        "source_seed": SOURCE_SEED, "query_seed": QUERY_SEED,
                        "adjacency": adjacency_layout(n, m, args.layout),
                        "z": stats_steps[0][4], "N_tot": stats_steps[0][2],
-                       "L": int(np.floor(np.log(n) / -np.log(np.sqrt(C)))),
+                       "L": int(stats_steps[0][5]),
                        "l2": "256 MB buffer written between queries (outside the timed intervals)",
                        "timing": "sum of per-query CUDA-event intervals on the query stream",
                        "parallelism": "sources sharded over ranks" if world > 1 else "1 GPU"},

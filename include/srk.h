@@ -63,10 +63,10 @@ extern "C" {
                                   p and q are then not used */
 #define SRK_OPT_LITERAL_SHUFFLE 4  /* single-source only: shuffle every
                                   target's walks too, by a keyed per-target
-                                  permutation (4-round Feistel, Philox round
-                                  functions), as Section 5.2 shuffles every
-                                  node's walks; slower (about 4 extra Philox
-                                  blocks per pair) */
+                                  permutation (unbalanced 4-round Feistel
+                                  with hash round functions), as Section 5.2
+                                  shuffles every node's walks; about 3.6x
+                                  slower than the default pairing */
 
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */

@@ -35,11 +35,24 @@
  * Optional literal shuffle of the targets' walks (every node's walks are
  * shuffled in Section 5.2; the default shuffles only the source's): target u
  * pairs walk pi_u(j) with source walk sigma[j], where pi_u is a keyed
- * permutation of 0..N_tot-1: a 4-round Feistel network on b bits (b the
- * smallest even number >= 2 with 2^b >= N_tot, halves of h = b/2 bits) with
- * round function F_r(x) = word 0 of Philox(counter (x, 0xFFFFFFF0 + r, u, s))
- * masked to h bits, (L, R) -> (R, L ^ F_r(R)) for r = 0..3, repeated on its
- * own output until the value falls below N_tot (cycle walking).
+ * permutation of 0..N_tot-1 (the identity when N_tot = 1): an unbalanced
+ * 4-round Feistel network on b bits, b the smallest integer with
+ * 2^b >= N_tot.  The value splits into A (the high floor(b/2) bits) and B
+ * (the low ceil(b/2) bits); a round maps (A, B) to (B, A ^ (F_r(B) mod
+ * 2^|A|)), so the two widths swap each round and are back after four.  The
+ * round function of target u is F_r(B) = h32(B ^ K_r(u)), with h32 the
+ * 32-bit finalizer "lowbias32" of C. Wellons ("Prospecting for hash
+ * functions", 2018):
+ *     x ^= x >> 16; x *= 0x7FEB352D; x ^= x >> 15; x *= 0x846CA68B; x ^= x >> 16
+ * and the 32-bit round key K_r(u) = low half of mix64(k_r ^ u), where mix64
+ * is the output function of SplitMix64 (Steele, Lea, Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014):
+ *     z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;
+ *     z *= 0x94D049BB133111EB; z ^= z >> 31
+ * and k_r = mix64(seed + (4 s + r + 1) 0x9E3779B97F4A7C15), the
+ * (4s + r + 1)-th output of SplitMix64 seeded with seed.  The network is
+ * applied to its own output until the value falls below N_tot (cycle
+ * walking; fewer than two passes on average since 2^b < 2 N_tot).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -102,25 +115,50 @@ int srko_walk(const int32_t *row_ptr, const int32_t *col, int32_t v,
     return len;
 }
 
+static uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+static uint32_t h32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return x;
+}
+
 /* pi_u(j): the keyed permutation of the literal target shuffle (see above). */
 int32_t srko_feistel(int32_t u, int32_t s, uint64_t seed, int32_t N, int32_t j) {
-    int b = 2;
-    while (((int64_t)1 << b) < (int64_t)N) b += 2;
-    const int h = b / 2;
-    const uint32_t mask = ((uint32_t)1 << h) - 1u;
-    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    if (N <= 1) return 0;
+    int b = 1;
+    while (((int64_t)1 << b) < (int64_t)N) ++b;
+    const int hi_bits = b / 2, lo_bits = b - hi_bits;
+    uint32_t K[4];
+    for (int r = 0; r < 4; ++r) {
+        const uint64_t k = mix64(seed + (4 * (uint64_t)(uint32_t)s + (uint64_t)r + 1) *
+                                            0x9E3779B97F4A7C15ull);
+        K[r] = (uint32_t)mix64(k ^ (uint64_t)(uint32_t)u);
+    }
     uint32_t v = (uint32_t)j;
     do {
-        uint32_t Lh = v >> h, Rh = v & mask;
-        for (uint32_t r = 0; r < 4; ++r) {
-            uint32_t ctr[4] = {Rh, 0xFFFFFFF0u + r, (uint32_t)u, (uint32_t)s};
-            uint32_t w[4];
-            srko_philox4x32_10(ctr, key, w);
-            uint32_t t = Lh ^ (w[0] & mask);
-            Lh = Rh;
-            Rh = t;
+        int na = hi_bits, nb = lo_bits;
+        uint32_t A = v >> lo_bits, B = v & (((uint32_t)1 << lo_bits) - 1u);
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t f = h32(B ^ K[r]);
+            const uint32_t C = A ^ (f & (((uint32_t)1 << na) - 1u));
+            A = B;
+            B = C;
+            const int t = na;
+            na = nb;
+            nb = t;
         }
-        v = (Lh << h) | Rh;
+        v = (A << nb) | B;
     } while (v >= (uint32_t)N);
     return (int32_t)v;
 }

@@ -340,42 +340,84 @@ namespace srk {
 
 // ---------------------------------------------------------------------------
 // Literal target shuffle: target u pairs its walk pi_u(j) with source walk
-// sigma[j].  pi_u is a 4-round Feistel network on b bits (b the smallest even
-// number >= 2 with 2^b >= N, halves of h = b/2 bits), round function
-// F_r(x) = word 0 of Philox(counter (x, 0xFFFFFFF0 + r, u, s)) masked to h
-// bits, (L, R) -> (R, L ^ F_r(R)), applied again until the value is below N
-// (cycle walking; the orbit of j < N returns below N within 2^b steps).
+// sigma[j].  pi_u is the identity when N = 1 and otherwise an unbalanced
+// 4-round Feistel network on b bits, b the smallest integer with 2^b >= N:
+// the value splits into A (high floor(b/2) bits) and B (low ceil(b/2) bits),
+// a round maps (A, B) to (B, A ^ (F_r(B) mod 2^|A|)) so the widths swap and
+// are back after four rounds, and the network is applied again until the
+// value is below N (cycle walking; fewer than two passes on average).  The
+// round function of target u is F_r(B) = h32(B ^ K_r(u)), h32 the 32-bit
+// finalizer "lowbias32" of C. Wellons (2018), with 32-bit round keys
+// K_r(u) = low half of mix64(k_r ^ u) and k_r = mix64(seed + (4 s + r + 1)
+// 0x9E3779B97F4A7C15), mix64 the output function of SplitMix64 (Steele, Lea,
+// Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
 struct FeistelShape {
-  int h;          // bits per half
-  uint32_t mask;  // 2^h - 1
+  int lo_bits, hi_bits;  // widths of B and A at the start
   int32_t N;
+  uint64_t k[4];         // round keys
 };
 
-__host__ __device__ __forceinline__ FeistelShape feistel_shape(int32_t N) {
-  int b = 2;
-  while (((int64_t)1 << b) < (int64_t)N) b += 2;
+__host__ __device__ __forceinline__ FeistelShape feistel_shape(int32_t N, uint64_t seed,
+                                                              uint32_t s) {
+  int b = 1;
+  while (((int64_t)1 << b) < (int64_t)N) ++b;
   FeistelShape f;
-  f.h = b / 2;
-  f.mask = (1u << f.h) - 1u;
+  f.hi_bits = b / 2;
+  f.lo_bits = b - f.hi_bits;
   f.N = N;
+  for (int r = 0; r < 4; ++r)
+    f.k[r] = mix64(seed + (4 * (uint64_t)s + (uint64_t)r + 1) * 0x9E3779B97F4A7C15ull);
   return f;
 }
 
-__device__ __forceinline__ int32_t feistel_pi(const RoundKeys &rk, const FeistelShape &f,
-                                              uint32_t u, uint32_t s, int32_t j) {
+__device__ __forceinline__ uint32_t h32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// The round keys K_r(u) of target u.
+struct FeistelKeys {
+  uint32_t K[4];
+};
+__device__ __forceinline__ FeistelKeys feistel_keys(const FeistelShape &f, uint32_t u) {
+  FeistelKeys k;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) k.K[r] = (uint32_t)mix64(f.k[r] ^ (uint64_t)u);
+  return k;
+}
+
+__device__ __forceinline__ int32_t feistel_pi(const FeistelShape &f, const FeistelKeys &K,
+                                              int32_t j) {
+  if (f.N <= 1) return 0;
   uint32_t v = (uint32_t)j;
-  const uint32_t limit = 1u << (2 * f.h);
+  const uint32_t limit = 1u << (f.lo_bits + f.hi_bits);  // an orbit is no longer
   for (uint32_t guard = 0; guard < limit; ++guard) {
-    uint32_t Lh = v >> f.h, Rh = v & f.mask;
-#pragma unroll 1
-    for (uint32_t r = 0; r < 4; ++r) {
-      uint32_t x0, x1, x2, x3;
-      philox(rk, Rh, 0xFFFFFFF0u + r, u, s, x0, x1, x2, x3);
-      const uint32_t t = Lh ^ (x0 & f.mask);
-      Lh = Rh;
-      Rh = t;
+    int na = f.hi_bits, nb = f.lo_bits;
+    uint32_t A = v >> f.lo_bits, B = v & ((1u << f.lo_bits) - 1u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t fr = h32(B ^ K.K[r]);
+      const uint32_t C = A ^ (fr & ((1u << na) - 1u));
+      A = B;
+      B = C;
+      const int t = na;
+      na = nb;
+      nb = t;
     }
-    v = (Lh << f.h) | Rh;
+    v = (A << nb) | B;
     if (v < (uint32_t)f.N) break;
   }
   return (int32_t)v;
@@ -396,19 +438,41 @@ __device__ __forceinline__ void walk_target_literal(
   bool live = false;
   int32_t a = 0, i = 1, p = 0, l2 = 0;
   uint32_t deg = 0, t = 0;
+  // The target walks of pairs [base, base + 64), computed by the whole warp
+  // (lane k: pair base + k in tw0, base + 32 + k in tw1) so that no lane
+  // evaluates the permutation alone while the others wait; packed as
+  // walk | (length << 24) (N_tot <= 2^24, L <= 255).
+  const int32_t lane = __popc(lanes_below);
+  const FeistelKeys K = feistel_keys(f, u);
+  auto batch = [&](int32_t first) -> uint32_t {
+    const int32_t q = first + lane;
+    if (q >= S.n_pairs) return 0u;
+    const uint32_t tw = (uint32_t)feistel_pi(f, K, S.pair_j[q]);
+    return tw | ((uint32_t)stratum_of(P, L, (int32_t)tw) << 24);
+  };
+  int32_t base = 0;
+  uint32_t tw0 = batch(0), tw1 = batch(32);
   for (;;) {
     const uint32_t idle = __ballot_sync(0xffffffffu, !live);
     if (idle) {
-      if (!live) {
-        a = next + __popc(idle & lanes_below);
-        if (a < S.n_pairs) {
-          t = (uint32_t)feistel_pi(rk, f, u, S.s, S.pair_j[a]);
-          l2 = stratum_of(P, L, (int32_t)t);
-          live = l2 >= 1;  // a length-0 target walk takes no step
-          i = 1;
-          p = beg_u;
-          deg = deg_u;
-        }
+      if (next >= base + 32) {  // warp-uniform: advance the batches
+        base += 32;
+        tw0 = tw1;
+        tw1 = batch(base + 32);
+      }
+      const int32_t an = next + __popc(idle & lanes_below);  // < base + 64
+      const int32_t k = an - base;
+      const uint32_t g0 = __shfl_sync(0xffffffffu, tw0, k & 31);
+      const uint32_t g1 = __shfl_sync(0xffffffffu, tw1, k & 31);
+      if (!live && an < S.n_pairs) {
+        a = an;
+        const uint32_t g = k < 32 ? g0 : g1;
+        t = g & 0xFFFFFFu;
+        l2 = (int32_t)(g >> 24);
+        live = l2 >= 1;  // a length-0 target walk takes no step
+        i = 1;
+        p = beg_u;
+        deg = deg_u;
       }
       next += __popc(idle);
     }

@@ -328,7 +328,9 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   S.Hc = A.Hc;
   S.n_pairs = cnt[1];
   S.s = (uint32_t)A.s;
-  const FeistelShape fs = feistel_shape(A.N_tot);
+  FeistelShape fs;
+  if constexpr (kLiteral)
+    fs = feistel_shape(A.N_tot, ((uint64_t)A.key1 << 32) | A.key0, (uint32_t)A.s);
   unsigned long long warp_steps = 0;
   // the active targets act[counter .. act_hi) (k_rows set the counter to the
   // range's first index and act_hi beside it); the outputs of the others
