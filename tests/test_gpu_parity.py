@@ -519,3 +519,40 @@ def test_degenerate_graphs_and_calls(srk):
         assert np.all(out == -5.0)
     finally:
         g.close()
+
+
+def test_concurrent_queries_on_streams_equal_serial(srk):
+    # the graph is read-only after load: queries of different sources on two
+    # streams (and a linearised pass on a third) may overlap on the GPU and
+    # still give the serial results bit for bit
+    import torch
+    from srk_inputs import lognormal_weights
+    dev = torch.device("cuda:0")
+    rp, col = rmat_graph(16)
+    n = rp.size - 1
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        sources = [11, 4242, 777, 60000, 5, 31337]
+        serial = []
+        for s in sources:
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+            srk.srk_single_source(g, s, C, 0.05, 9, out)
+            torch.cuda.synchronize()
+            serial.append(out.clone())
+        w = torch.from_numpy(lognormal_weights(col.size, seed=3)).to(dev)
+        lin_ref = torch.empty(n, dtype=torch.float32, device=dev)
+        srk.srk_linear_fwd(g, w, 3, C, 6, lin_ref, keep_context=False)
+        torch.cuda.synchronize()
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in sources]
+        lin = torch.empty(n, dtype=torch.float32, device=dev)
+        for k, s in enumerate(sources):
+            srk.srk_single_source(g, s, C, 0.05, 9, outs[k], stream=streams[k % 2])
+            if k == 2:
+                srk.srk_linear_fwd(g, w, 3, C, 6, lin, keep_context=False, stream=streams[2])
+        torch.cuda.synchronize()
+        for a, b in zip(serial, outs):
+            assert torch.equal(a, b)
+        assert torch.equal(lin, lin_ref)
+    finally:
+        g.close()
