@@ -100,6 +100,8 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
   }
   if (!(p >= 1.0) || !(q >= 1.0) || !isfinite(p) || !isfinite(q))
     return fail(SRK_EINVAL, "p = %g and q = %g must be >= 1", p, q);
+  if (z_ovr != 0.0 && !(z_ovr > 0.0 && isfinite(z_ovr)))
+    return fail(SRK_EINVAL, "z_override = %g must be 0 (none) or positive and finite", z_ovr);
   const double rc = sqrt(c);
   double z;
   if (z_ovr > 0.0) {

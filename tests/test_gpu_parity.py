@@ -246,6 +246,12 @@ def test_invalid_arguments_are_rejected(srk):
             srk.srk_single_source(g, 0, 0.6, 0.5, 1, out, L_override=srk.SRK_MAX_LEN + 1)
         with pytest.raises(srk.SrkError):
             srk.srk_single_source(g, 0, 0.6, 0.5, 1, out, p=0.5)
+        for bad in (float("nan"), -3.0, float("inf")):
+            with pytest.raises(srk.SrkError) as e:
+                srk.srk_single_source(g, 0, 0.6, 0.5, 1, out, z_override=bad)
+            assert e.value.code == srk.SRK_EINVAL
+        with pytest.raises(srk.SrkError):
+            srk.srk_single_source(g, 0, 0.6, float("nan"), 1, out)
     finally:
         g.close()
     # malformed CSRs are refused at load time (checked by an in-bounds kernel)
