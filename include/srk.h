@@ -97,7 +97,8 @@ typedef struct srk_stats {
 /* Query options; pass NULL for the paper's defaults. */
 typedef struct srk_opts {
     double   z_override;   /* > 0: use as z instead of ln(2n^q)/(2(eps-3/n^p)^2);
-                              eps is then not used */
+                              eps is then not used.  0: the paper's z; NaN,
+                              negative or infinite: SRK_EINVAL */
     int32_t  L_override;   /* >= 0: truncation length instead of
                               floor(p ln n / ln(1/sqrt(c))); < 0: paper */
     int32_t  flags;        /* SRK_OPT_* bits (SRK_OPT_NO_GRAPH: multi-source only) */
@@ -170,7 +171,9 @@ int srk_graph_info(const srk_graph *g, int32_t *n, int64_t *m);
  * Walk lengths: N_l = ceil(z sqrt(c)^l (1 - sqrt(c))) walks of length l for
  * l = 0..L, L = floor(p ln n / ln(1/sqrt c)).  The source's N_tot walks are
  * shuffled by one Fisher-Yates permutation; pair j joins source walk sigma(j)
- * with target walk j.  A pair meets when both walks are at the same node at
+ * with target walk j (with SRK_OPT_LITERAL_SHUFFLE, target u's walk pi_u(j),
+ * pi_u a keyed permutation of its own).  A pair meets when both walks are at
+ * the same node at
  * the same step i >= 1; it counts once.  A walk stops early at a node without
  * in-neighbours.  Returns SRK_EINVAL for s, c, eps, p, q out of range, or
  * when L > SRK_MAX_LEN, N_tot > SRK_MAX_WALKS or sum_l l N_l >= 2^31.
@@ -199,7 +202,8 @@ int srk_single_source(const srk_graph *g, int32_t s, double c, double eps,
  * kernel's launch shape is picked per graph by timing the candidate shapes on
  * the first items of the first call (kept in the handle).  The call
  * synchronises the stream at the end of every batch.  opt->step_counts must
- * be NULL; opt->stats, if set, receives totals over all sources.
+ * be NULL, and target ranges and SRK_OPT_LITERAL_SHUFFLE are refused
+ * (SRK_EINVAL); opt->stats, if set, receives totals over all sources.
  */
 int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
                      double c, const double *eps, uint64_t seed,
@@ -222,15 +226,14 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
  *   ctx    : NULL, or receives the context the backward needs (device
  *            memory for P, the vectors P^t e_s and the partial sums, about
  *            (2L + 5) n + 2m words); release it with srk_linear_ctx_free.
- * The first call on a graph also builds and keeps in the handle a transpose
- * of the graph (out-lists in edge order) and the edges' owners, 3m + n words,
- * released by srk_graph_free.  Results do not depend on timing: every sum is
- * taken in a fixed order.
  *            The context refers to g, which must outlive it.
  *   cuda_stream : stream to run on; the call synchronises it (to report
  *            non-positive weights as SRK_EINVAL).
- * Arithmetic is FP32; P v is accumulated in FP64 atomics (order-independent
- * up to FP64 rounding) and P^T v by fixed-order warp reductions.
+ * The first call on a graph also builds and keeps in the handle a transpose
+ * of the graph (out-lists in edge order) and the edges' owners, about
+ * 3m + 3n words, released by srk_graph_free.  Arithmetic is FP32; P v and
+ * P^T v are gathers along out-lists and in-lists, every sum taken in a fixed
+ * order, so results are bitwise reproducible.
  */
 int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s, double c,
                    int32_t L, float *s_out, srk_linear_ctx **ctx, void *cuda_stream);
@@ -317,7 +320,8 @@ int srk_probe_gather_ex(const int32_t *data, int64_t n, int64_t iters, uint32_t 
  *   with shortest-estimated-work-first service.  The estimate is (nodes with
  *   in-neighbours) x N_tot x 0.8 walk steps per request (0 when the source
  *   has no in-neighbours), divided by the rate at which completed requests
- *   got through their estimate (exponential average, starting at 5e10/s).  Copies each graph's row_ptr to the host once.
+ *   got through their estimate (exponential average, starting at 5e10/s).
+ *   Copies each graph's row_ptr to the host once.
  * srk_server_submit -- enqueue one srk_single_source query on graph index
  *   `graph`.  The request is admitted if the memory it needs fits in what the
  *   budget leaves (and, with a latency target, its estimated finish fits the
