@@ -369,8 +369,9 @@ def test_warmup_rule_bit_exact(srk):
 
 @pytest.mark.parametrize("z,L", [(2000.0, 32), (1.0, 0), (37.0, 5)])
 def test_literal_shuffle_bit_exact(srk, z, L):
-    # every target's walks shuffled by its own keyed permutation (Section 4.2
-    # read literally): Feistel domains of 4, 64 and 4096 with cycle walking
+    # every target's walks shuffled by its own keyed permutation (Section 5.2
+    # read literally): N_tot = 2018 (an 11-bit network, unequal halves, cycle
+    # walking), N_tot = 1 (the identity) and N_tot = 33 (6 bits)
     rp, col = er_graph(1000, 5.0, 1)
     for s, seed in ((0, 1), (17, 9)):
         gpu = gpu_query(srk, rp, col, s, 0.1, seed, z_override=z, L_override=L,
