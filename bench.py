@@ -230,13 +230,18 @@ def adjacency_layout(n, m, forced):
 
 
 def kernel_source_sha256():
-    """sha256 over the sources the target-walk kernel is compiled from (the
-    kernel file, then the device header), in that order."""
+    """sha256 over the code the target-walk kernel is compiled from (the kernel
+    file, then the device header), with comments and whitespace removed, so
+    that an edit of the prose alone keeps a traffic record valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in ("srk_query.cu", "srk_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2304_04015_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2304_04015_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -323,13 +323,17 @@ static void launch_targets_t(int shape, int grid, int block, size_t smem, cudaSt
                              const BatchArgs &A, const int32_t *act, int32_t n_act,
                              const int32_t *act_src, const int32_t *n_act_src,
                              unsigned long long *ctr, int64_t limit, int32_t rw) {
+#define SRK_KB_LAUNCH(B, M)                                                                  \
+  kb_target_walks<B, M, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, \
+                                                            ctr, limit, rw)
   switch (shape) {
-    case 0: kb_target_walks<256, 8, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 1: kb_target_walks<512, 4, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 2: kb_target_walks<128, 16, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    case 3: kb_target_walks<1024, 2, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
-    default: kb_target_walks<256, 6, kLayout><<<grid, block, smem, st>>>(A, act, n_act, act_src, n_act_src, ctr, limit, rw); break;
+    case 0: SRK_KB_LAUNCH(256, 8); break;
+    case 1: SRK_KB_LAUNCH(512, 4); break;
+    case 2: SRK_KB_LAUNCH(128, 16); break;
+    case 3: SRK_KB_LAUNCH(1024, 2); break;
+    default: SRK_KB_LAUNCH(256, 6); break;
   }
+#undef SRK_KB_LAUNCH
 }
 
 static void launch_targets(int layout, int shape, int sms, cudaStream_t st, const BatchArgs &A,
@@ -446,7 +450,8 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     int Lmax = 0;
     for (int32_t b = i0; b < i1; ++b) Lmax = std::max(Lmax, tabs[(size_t)b].L);
     const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
-                        align256(sizeof(int64_t) * (kb + 1)) + align256(sizeof(int32_t) * (kb + 1)) +
+                        align256(sizeof(int64_t) * (kb + 1)) +
+                        align256(sizeof(int32_t) * (kb + 1)) +
                         align256(sizeof(unsigned long long) * (kb + 1));
     char *base = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&base, head + need, mp, st);

@@ -325,7 +325,8 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
     const size_t cb = sizeof(int32_t) * (size_t)(m > 0 ? m : 1);
     if ((e = cudaMalloc(&g->own_row_ptr, rb)) != cudaSuccess ||
         (e = cudaMalloc(&g->own_col, cb)) != cudaSuccess ||
-        (edge_w && (e = cudaMalloc(&g->own_w, sizeof(float) * (size_t)(m > 0 ? m : 1))) != cudaSuccess)) {
+        (edge_w && (e = cudaMalloc(&g->own_w, sizeof(float) * (size_t)(m > 0 ? m : 1))) !=
+                       cudaSuccess)) {
       int rc = cuda_fail(e, "srk_graph_load: device allocation");
       srk_graph_free(g);
       return rc;
@@ -424,7 +425,9 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
     e = cudaGetLastError();
     if (e == cudaSuccess)
       e = cudaMemcpy(&n_act, off + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && (e = cudaMalloc(&g->act, sizeof(int32_t) * (size_t)(n_act > 0 ? n_act : 1))) == cudaSuccess) {
+    if (e == cudaSuccess &&
+        (e = cudaMalloc(&g->act, sizeof(int32_t) * (size_t)(n_act > 0 ? n_act : 1))) ==
+            cudaSuccess) {
       k_active_scatter<<<sm_count(dev) * 4, 256>>>(flag, off, n, g->act);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaDeviceSynchronize();

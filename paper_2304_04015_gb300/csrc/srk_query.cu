@@ -28,9 +28,10 @@ namespace srk {
 // Walk r of the source has length l = stratum(r).  Step i >= 1 draws 64 bits
 // from Philox counter ((i-1)>>1, r, s, s), word pair 2*((i-1)&1) (high, low),
 // and moves to I(x)[floor(R * |I(x)| / 2^64)]; it stops early at a node with
-// no in-neighbours.  Walks run on the packed adjacency (degree, then the
-// in-neighbours' positions), so nodes are identified by their position.  The same thread computes Fisher-Yates draw t = r,
-// k_t = floor(R * (t+1) / 2^64) with R from counter (t>>1, ~0, ~0, s).
+// no in-neighbours.  Walks run on the graph's adjacency layout (a packed copy
+// in which nodes are identified by their position, or the CSR itself).  The
+// same thread computes Fisher-Yates draw t = r, k_t = floor(R * (t+1) / 2^64)
+// with R from counter (t>>1, ~0, ~0, s).
 template <int kLayout>
 __global__ void __launch_bounds__(256)
 k_source_walks(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,

@@ -160,7 +160,8 @@ extern "C" int srk_server_create(const srk_graph *const *graphs, int32_t n_graph
   if (!out) return fail(SRK_EINVAL, "out is null");
   *out = nullptr;
   if (!graphs || n_graphs < 1) return fail(SRK_EINVAL, "no graphs");
-  if (n_workers < 1 || n_workers > 64) return fail(SRK_EINVAL, "n_workers = %d outside [1, 64]", n_workers);
+  if (n_workers < 1 || n_workers > 64)
+    return fail(SRK_EINVAL, "n_workers = %d outside [1, 64]", n_workers);
   if (mem_budget == 0) return fail(SRK_EINVAL, "mem_budget must be positive");
   for (int32_t i = 0; i < n_graphs; ++i)
     if (!graphs[i]) return fail(SRK_EINVAL, "graph %d is null", i);
