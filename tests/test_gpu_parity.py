@@ -563,3 +563,29 @@ def test_concurrent_queries_on_streams_equal_serial(srk):
         assert torch.equal(lin, lin_ref)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("opts", [dict(warmup_rule=True), dict(p=1.5, q=2.0),
+                                  dict(z_override=900.0, L_override=7)])
+def test_multi_source_options_equal_single_queries(srk, opts):
+    # the batched path applies the same sample-count options per source
+    import torch
+    dev = torch.device("cuda:0")
+    rp, col = er_graph(1000, 5.0, 1)
+    n = rp.size - 1
+    sources = [0, 17, 503, 999]
+    eps = [0.3, 0.25, 0.35, 0.3]
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        multi = torch.empty((len(sources), n), dtype=torch.float64, device=dev)
+        mc = torch.empty((len(sources), n), dtype=torch.int32, device=dev)
+        srk.srk_multi_source(g, sources, C, eps, 23, multi, mc, **opts)
+        one = torch.empty(n, dtype=torch.float64, device=dev)
+        oc = torch.empty(n, dtype=torch.int32, device=dev)
+        for i, s in enumerate(sources):
+            srk.srk_single_source(g, s, C, eps[i], 23, one, oc, **opts)
+            torch.cuda.synchronize()
+            assert torch.equal(one, multi[i]) and torch.equal(oc, mc[i])
+        assert int(mc.sum()) > 0
+    finally:
+        g.close()
