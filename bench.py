@@ -219,16 +219,6 @@ def variant_suffix(args):
     return ("_literal" if args.literal_shuffle else "") + ("_warmup" if args.warmup_rule else "")
 
 
-def adjacency_layout(n, m, forced):
-    """The adjacency layout srk_graph_load picks (or the forced one)."""
-    if forced:
-        return forced
-    pb = 1
-    while pb < 31 and (1 << pb) < n + m:
-        pb += 1
-    return "narrow" if pb <= 26 else ("csr" if pb == 27 else "wide")
-
-
 def kernel_source_sha256():
     """sha256 over the code the target-walk kernel is compiled from (the kernel
     file, then the device header), with comments and whitespace removed, so
@@ -388,7 +378,7 @@ def run_batch(args, rank, world):
             "source_in_degrees": [int(deg[s]) for s in sources], "eps": eps,
             "target_steps": st.target_steps, "walk_steps_per_s": st.target_steps / t_batch,
             "batch_shape": st.batch_shape, "graph_gen_s": t_gen,
-            "adjacency": adjacency_layout(n, m, args.layout),
+            "adjacency": srk.srk_graph_layout(g),
             "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
     print(json.dumps(line), flush=True)
@@ -802,7 +792,7 @@ def main():
                        "(0.57,0.19,0.19,0.05), dedup, no self-loops, seed %d" % GRAPH_SEED,
                        "n": n, "m": m, "c": C, "eps": EPS, "sources": N_SOURCES,
                        "source_seed": SOURCE_SEED, "query_seed": QUERY_SEED,
-                       "adjacency": adjacency_layout(n, m, args.layout),
+                       "adjacency": srk.srk_graph_layout(g),
                        "z": stats_steps[0][4], "N_tot": stats_steps[0][2],
                        "L": int(stats_steps[0][5]),
                        "l2": "256 MB buffer written between queries (outside the timed intervals)",

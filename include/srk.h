@@ -154,6 +154,10 @@ int srk_graph_free(srk_graph *g);
 /* srk_graph_info -- n and m of a loaded graph (either pointer may be NULL). */
 int srk_graph_info(const srk_graph *g, int32_t *n, int64_t *m);
 
+/* srk_graph_layout -- the adjacency layout the walks read (see srk_graph_load):
+ * *layout = SRK_ADJ_NARROW, SRK_ADJ_WIDE or SRK_ADJ_CSR. */
+int srk_graph_layout(const srk_graph *g, int32_t *layout);
+
 /*
  * srk_single_source -- estimate s~(s, u) for every node u (Algorithms 1, 2).
  *   s     : query source, 0 <= s < n.

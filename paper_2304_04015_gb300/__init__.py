@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "SrkError", "SrkOpts", "SrkStats", "Graph",
-    "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_single_source",
+    "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout", "srk_single_source",
     "srk_multi_source", "srk_single_source_noalloc", "srk_probe_gather",
     "srk_probe_gather_ex", "SRK_PROBE_DEFAULT", "SRK_PROBE_CG", "SRK_PROBE_NC", "SRK_PROBE_CA",
     "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free", "LinearContext",
@@ -85,6 +85,7 @@ _lib.srk_single_source_noalloc.argtypes = _lib.srk_single_source.argtypes
 _lib.srk_multi_source.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double,
                                   _vp, ctypes.c_uint64, ctypes.POINTER(SrkOpts),
                                   _vp, _vp, _vp]
+_lib.srk_graph_layout.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
 _lib.srk_probe_gather.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
                                   _vp, ctypes.POINTER(ctypes.c_int64), _vp]
 _lib.srk_probe_gather_ex.argtypes = [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32,
@@ -114,7 +115,7 @@ _lib.srk_server_drain.argtypes = [_vp]
 _lib.srk_server_stats.argtypes = [_vp, ctypes.POINTER(SrkServerReport)]
 _lib.srk_server_destroy.argtypes = [_vp]
 _lib.srk_last_error.restype = ctypes.c_char_p
-for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info",
+for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout",
            "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
            "srk_probe_gather", "srk_probe_gather_ex", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free",
            "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
@@ -226,6 +227,13 @@ def srk_graph_load(row_ptr, col, n: Optional[int] = None, m: Optional[int] = Non
 
 def srk_graph_free(g: Graph) -> None:
     g.close()
+
+
+def srk_graph_layout(g: Graph) -> str:
+    """The adjacency layout the walks read: "narrow", "wide" or "csr"."""
+    v = ctypes.c_int32()
+    _check(_lib.srk_graph_layout(g.handle, ctypes.byref(v)))
+    return {SRK_ADJ_NARROW: "narrow", SRK_ADJ_WIDE: "wide", SRK_ADJ_CSR: "csr"}[v.value]
 
 
 def srk_graph_info(g: Graph):

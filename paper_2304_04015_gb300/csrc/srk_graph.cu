@@ -260,6 +260,12 @@ using namespace srk;
 
 extern "C" const char *srk_last_error(void) { return g_last_error.c_str(); }
 
+extern "C" int srk_graph_layout(const srk_graph *g, int32_t *layout) {
+  if (!g || !layout) return fail(SRK_EINVAL, "null argument");
+  *layout = g->layout == 1 ? SRK_ADJ_WIDE : g->layout == 2 ? SRK_ADJ_CSR : SRK_ADJ_NARROW;
+  return SRK_OK;
+}
+
 extern "C" int srk_graph_info(const srk_graph *g, int32_t *n, int64_t *m) {
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (n) *n = g->n;

@@ -51,6 +51,7 @@ def test_batching_workload_rmat24_sampled_targets(srk):
     deg = np.diff(rp)
     assert deg[sources[0]] > 1000 and deg[sources[2]] == 0
     g = srk.srk_graph_load(rp_d, col_d)
+    assert srk.srk_graph_layout(g) == "wide"   # 29 position bits
     try:
         scores = torch.empty((3, n), dtype=torch.float64, device=dev)
         counts = torch.empty((3, n), dtype=torch.int32, device=dev)

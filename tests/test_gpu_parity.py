@@ -456,6 +456,7 @@ def test_wide_adjacency_layout_bit_exact(srk):
         for layout in ("narrow", "wide", "csr"):
             g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
                                    layout=layout)
+            assert srk.srk_graph_layout(g) == layout
             try:
                 sc = torch.empty(n, dtype=torch.float64, device=dev)
                 cn = torch.empty(n, dtype=torch.int32, device=dev)
@@ -478,6 +479,10 @@ def test_wide_adjacency_layout_bit_exact(srk):
             for a, b in zip(outs[0], other):
                 assert np.array_equal(a, b)
         assert outs[1][1].sum() > 0
+    # small graphs default to 4-byte entries
+    g = srk.srk_graph_load(*er_graph(1000, 5.0, 1))
+    assert srk.srk_graph_layout(g) == "narrow"
+    g.close()
     # and the wide layout against the oracle directly
     rp, col = er_graph(1000, 5.0, 1)
     g = srk.srk_graph_load(rp, col, layout="wide")
