@@ -220,13 +220,14 @@ def variant_suffix(args):
 
 
 def kernel_source_sha256():
-    """sha256 over the code the target-walk kernel is compiled from (the kernel
-    file, then the device header), with comments and whitespace removed, so
-    that an edit of the prose alone keeps a traffic record valid."""
+    """sha256 over the code the target-walk kernel is compiled from and the
+    code that lays out the adjacency it reads (the kernel file, the device
+    header, the graph loader), with comments and whitespace removed, so that
+    an edit of the prose alone keeps a traffic record valid."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("srk_query.cu", "srk_device.cuh"):
+    for name in ("srk_query.cu", "srk_device.cuh", "srk_graph.cu"):
         with open(os.path.join(ROOT, "paper_2304_04015_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)

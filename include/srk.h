@@ -128,13 +128,16 @@ typedef struct srk_opts {
  *                  are copied.  SRK_VALIDATE is accepted and implied.
  *                  SRK_ADJ_NARROW / SRK_ADJ_WIDE / SRK_ADJ_CSR force the
  *                  adjacency layout the walks read: a packed copy with
- *                  4-byte entries carrying a degree code of
- *                  32 - ceil(log2(n + m)) bits, a packed copy with 8-byte
- *                  entries carrying the full degree, or row_ptr and col
- *                  themselves (no copy).  By default: 4-byte entries while
- *                  n + m <= 2^26, the CSR while n + m <= 2^27, 8-byte
- *                  entries beyond.  Results do not depend on the layout;
- *                  giving more than one of the flags is SRK_EINVAL.
+ *                  4-byte entries carrying a degree code of 32 - b bits,
+ *                  2^b >= n + m + H, where the H nodes whose degree the code
+ *                  cannot hold keep their degree in a header (n + m + H
+ *                  words plus n positions; SRK_EINVAL if n + m + H >= 2^31);
+ *                  a packed copy with 8-byte entries carrying the full
+ *                  degree (2 (n + m) words); or row_ptr and col themselves
+ *                  (no copy).  By default: 4-byte entries while
+ *                  n + m <= 2^28, 8-byte entries beyond.  Results do not
+ *                  depend on the layout; giving more than one of the flags
+ *                  is SRK_EINVAL.
  * The CSR invariants (row_ptr[0] = 0, row_ptr[n] = m, row_ptr non-decreasing,
  * 0 <= col < n) are always checked on the device before the handle is
  * returned; a violation returns SRK_EINVAL.  The walk kernels rely on them.

@@ -46,6 +46,7 @@ struct BatchArgs {
   const int32_t *row_ptr;
   const int32_t *col;
   const uint32_t *adj;
+  const int32_t *npos;
   int32_t pos_bits;
   uint32_t key0, key1;
 };
@@ -72,16 +73,17 @@ __device__ __forceinline__ int find_source(const int64_t *off, int k, int64_t g)
 template <int kLayout>
 __global__ void __launch_bounds__(256) kb_source_walks(const __grid_constant__ BatchArgs A) {
   const RoundKeys rk = round_keys(A.key0, A.key1);
-  const auto G = adj_view<kLayout>(A.adj, A.pos_bits, A.row_ptr, A.col);
+  const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   SRK_BATCH_LOOP(A, {
     const QueryTab &t = *S_.tab;
     const uint32_t s = (uint32_t)S_.s;
-    const int32_t p_s = node_pos(G, A.row_ptr, S_.s);
+    uint32_t deg_s = 0;
+    const int32_t b_s = node_start(G, A.row_ptr, S_.s, deg_s);
     const int Ls = S_.L > 0 ? S_.L : 1;
     S_.w.grp_cnt[r_] = 0;
     S_.w.kdraw[r_] = (r_ >= 1) ? fy_draw(rk, s, r_) : 0;
     const int len = stratum_of(t.P, S_.L, r_);
-    const int eff = source_walk(rk, G, s, p_s, header_deg(G, p_s), r_, len,
+    const int eff = source_walk(rk, G, s, b_s, deg_s, r_, len,
                                 S_.w.spos + (int64_t)r_ * Ls);
     S_.w.seff[r_] = eff;
     atomicAdd(small_view(S_.w.small).ctr + 1, (unsigned long long)eff);
@@ -252,7 +254,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const auto G = adj_view<kLayout>(A.adj, A.pos_bits, A.row_ptr, A.col);
+  const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   int32_t *my_cnt = rows + (2 * wib) * row_words;
   int32_t *my_R = my_cnt + row_words;
   const int64_t n_items = (int64_t)(*n_act_src_p) * n_act;
@@ -293,9 +295,9 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     if (u == A.src[i].s) continue;  // prefilled with 1
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
-    const int32_t beg_u = node_pos(G, A.row_ptr, u);
-    walk_target(rk, G, ctx[wib], (uint32_t)u, beg_u, header_deg(G, beg_u), lanes_below, c, W,
-                st);
+    uint32_t deg_u = 0;
+    const int32_t b_u = node_start(G, A.row_ptr, u, deg_u);
+    walk_target(rk, G, ctx[wib], (uint32_t)u, b_u, deg_u, lanes_below, c, W, st);
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
       st += __shfl_xor_sync(0xffffffffu, st, off);
@@ -504,6 +506,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     A.row_ptr = g->row_ptr;
     A.col = g->col;
     A.adj = g->adj;
+    A.npos = g->npos;
     A.pos_bits = g->pos_bits;
     A.key0 = (uint32_t)seed;
     A.key1 = (uint32_t)(seed >> 32);

@@ -107,46 +107,69 @@ __host__ __device__ __forceinline__ Small small_view(int32_t *base) {
   return s;
 }
 
-// The packed adjacency: a node at position p has degree adj[p]; entry k of
-// its list, adj[p + 1 + k], is (degree code << pb) | position of the k-th
-// in-neighbour, the code being the degree when it is below dmax.
+// The walks hold the node they are at as (base, deg): the index of its
+// list's first entry and its in-degree.  Each layout supplies
+//   adj_entry(G, base, deg, hi, lo): the entry a step reads with the 64-bit
+//       draw (hi, lo), the in-neighbour of index floor(R deg / 2^64);
+//   entry_pos(G, e): the identity of the node that entry names (what the hit
+//       table holds);
+//   entry_next(G, e, x, deg): base (returned) and degree of that node x;
+//   node_start(G, row_ptr, v, deg): base and degree of node v, by id.
+
+// The packed adjacency with 4-byte entries: node v's identity is its position
+// pos[v]; a node of degree d < dmax has the word d there and its list right
+// after it; a hub (d >= dmax) has {d, list offset} at an even position of the
+// hub region; entry k of a list is (min(|I(y)|, dmax) << pb) | pos[y].
 struct Adj {
   const uint32_t *adj;
+  const int32_t *pos;
   int pb;
   uint32_t pmask, dmax;
 };
 
-__host__ __device__ __forceinline__ Adj make_adj(const uint32_t *adj, int pb) {
+__host__ __device__ __forceinline__ Adj make_adj(const uint32_t *adj, const int32_t *pos,
+                                                 int pb) {
   Adj a;
   a.adj = adj;
+  a.pos = pos;
   a.pb = pb;
   a.pmask = (uint32_t)((1ull << pb) - 1ull);
   a.dmax = (uint32_t)((1ull << (32 - pb)) - 1ull);
   return a;
 }
 
-// The entry a step from the node at position p (degree deg > 0) reads with
-// the 64-bit draw (hi, lo): the in-neighbour of index floor(R deg / 2^64).
-__device__ __forceinline__ uint32_t adj_entry(const Adj &G, int32_t p, uint32_t deg,
+__device__ __forceinline__ uint32_t adj_entry(const Adj &G, int32_t base, uint32_t deg,
                                               uint32_t hi, uint32_t lo) {
-  return G.adj[p + 1 + (int32_t)draw_index(hi, lo, deg)];
+  return G.adj[base + (int32_t)draw_index(hi, lo, deg)];
 }
 __device__ __forceinline__ int32_t entry_pos(const Adj &G, uint32_t e) {
   return (int32_t)(e & G.pmask);
 }
-// Degree of the node x = entry_pos(e): from the entry, or from x's header
-// when the degree does not fit the entry's code.
-__device__ __forceinline__ uint32_t entry_deg(const Adj &G, uint32_t e, int32_t x) {
+// The degree comes with the entry unless x is a hub; a hub's two header
+// words are read together (its position is even).
+__device__ __forceinline__ int32_t entry_next(const Adj &G, uint32_t e, int32_t x,
+                                              uint32_t &deg) {
   const uint32_t code = e >> G.pb;
-  return code < G.dmax ? code : G.adj[x];
+  if (code < G.dmax) {
+    deg = code;
+    return x + 1;
+  }
+  const uint2 h = *reinterpret_cast<const uint2 *>(G.adj + x);
+  deg = h.x;
+  return (int32_t)h.y;
 }
-__device__ __forceinline__ uint32_t header_deg(const Adj &G, int32_t p) { return G.adj[p]; }
+__device__ __forceinline__ int32_t node_start(const Adj &G, const int32_t *, int32_t v,
+                                              uint32_t &deg) {
+  const int32_t x = G.pos[v];
+  deg = G.adj[x];
+  return deg < G.dmax ? x + 1 : (int32_t)G.adj[x + 1];
+}
 
 // The wide packed adjacency, for graphs whose positions need more than 27
 // bits (the degree code of a 32-bit entry would then be too small to spare
-// most steps a second random read): the same positions, with 8-byte words.
-// adj[p] = {0, |I(v)|} at a node's position p; entry k of its list,
-// adj[p + 1 + k], is {position of the k-th in-neighbour y, |I(y)|}.
+// most steps a second random read): 8-byte words at positions
+// pos(v) = v + row_ptr[v], adj[pos(v)] = {0, |I(v)|}; entry k of v's list,
+// adj[pos(v) + 1 + k], is {position of the k-th in-neighbour y, |I(y)|}.
 struct AdjW {
   const uint2 *adj;
 };
@@ -156,71 +179,76 @@ __host__ __device__ __forceinline__ AdjW make_adjw(const uint32_t *words) {
   a.adj = reinterpret_cast<const uint2 *>(words);
   return a;
 }
-__device__ __forceinline__ uint2 adj_entry(const AdjW &G, int32_t p, uint32_t deg,
+__device__ __forceinline__ uint2 adj_entry(const AdjW &G, int32_t base, uint32_t deg,
                                            uint32_t hi, uint32_t lo) {
-  return G.adj[p + 1 + (int32_t)draw_index(hi, lo, deg)];
+  return G.adj[base + (int32_t)draw_index(hi, lo, deg)];
 }
 __device__ __forceinline__ int32_t entry_pos(const AdjW &, uint2 e) { return (int32_t)e.x; }
-__device__ __forceinline__ uint32_t entry_deg(const AdjW &, uint2 e, int32_t) { return e.y; }
-__device__ __forceinline__ uint32_t header_deg(const AdjW &G, int32_t p) { return G.adj[p].y; }
+__device__ __forceinline__ int32_t entry_next(const AdjW &, uint2 e, int32_t x,
+                                              uint32_t &deg) {
+  deg = e.y;
+  return x + 1;
+}
+__device__ __forceinline__ int32_t node_start(const AdjW &G, const int32_t *row_ptr,
+                                              int32_t v, uint32_t &deg) {
+  const int32_t x = v + row_ptr[v];
+  deg = G.adj[x].y;
+  return x + 1;
+}
 
-// The CSR layout: nodes are their own ids, a step reads row_ptr[x] and
-// row_ptr[x+1] (the list and its degree) and one col entry.
+// The CSR layout: nodes are their own ids; landing on x reads row_ptr[x] and
+// row_ptr[x+1] (the list and its degree), a step one col entry.
 struct AdjC {
   const int32_t *row_ptr;
   const int32_t *col;
 };
-__device__ __forceinline__ uint32_t header_deg(const AdjC &G, int32_t v) {
-  return (uint32_t)(G.row_ptr[v + 1] - G.row_ptr[v]);
-}
-__device__ __forceinline__ int32_t adj_entry(const AdjC &G, int32_t v, uint32_t deg,
+__device__ __forceinline__ int32_t adj_entry(const AdjC &G, int32_t base, uint32_t deg,
                                              uint32_t hi, uint32_t lo) {
-  return G.col[G.row_ptr[v] + (int32_t)draw_index(hi, lo, deg)];
+  return G.col[base + (int32_t)draw_index(hi, lo, deg)];
 }
 __device__ __forceinline__ int32_t entry_pos(const AdjC &, int32_t e) { return e; }
-__device__ __forceinline__ uint32_t entry_deg(const AdjC &G, int32_t, int32_t x) {
-  return header_deg(G, x);
+__device__ __forceinline__ int32_t entry_next(const AdjC &G, int32_t, int32_t x,
+                                              uint32_t &deg) {
+  const int32_t b = G.row_ptr[x];
+  deg = (uint32_t)(G.row_ptr[x + 1] - b);
+  return b;
 }
-
-// The identity of node v inside the walk kernels: its position in the
-// packed layouts, its id in the CSR layout.
-__device__ __forceinline__ int32_t node_pos(const Adj &, const int32_t *row_ptr, int32_t v) {
-  return v + row_ptr[v];
+__device__ __forceinline__ int32_t node_start(const AdjC &G, const int32_t *, int32_t v,
+                                              uint32_t &deg) {
+  const int32_t b = G.row_ptr[v];
+  deg = (uint32_t)(G.row_ptr[v + 1] - b);
+  return b;
 }
-__device__ __forceinline__ int32_t node_pos(const AdjW &, const int32_t *row_ptr, int32_t v) {
-  return v + row_ptr[v];
-}
-__device__ __forceinline__ int32_t node_pos(const AdjC &, const int32_t *, int32_t v) { return v; }
 
 // Adjacency layouts (srk_graph::layout).
 constexpr int kNarrow = 0, kWide = 1, kCsr = 2;
 
 // The view of a graph's adjacency in layout kLayout.
 template <int kLayout>
-__device__ __forceinline__ auto adj_view(const uint32_t *words, int pb, const int32_t *row_ptr,
-                                         const int32_t *col) {
+__device__ __forceinline__ auto adj_view(const uint32_t *words, const int32_t *pos, int pb,
+                                         const int32_t *row_ptr, const int32_t *col) {
   if constexpr (kLayout == kWide) return make_adjw(words);
   else if constexpr (kLayout == kCsr) return AdjC{row_ptr, col};
-  else return make_adj(words, pb);
+  else return make_adj(words, pos, pb);
 }
 
-// Source walk r of length len from the node at position p_s (degree deg_s):
-// writes the position at step i to out[i-1]; returns the steps taken.  Step
-// i draws from Philox counter ((i-1)>>1, r, s, s), words 2((i-1)&1), +1.
+// Source walk r of length len from s (list base b_s, degree deg_s): writes
+// the identity of the node at step i to out[i-1]; returns the steps taken.
+// Step i draws from Philox counter ((i-1)>>1, r, s, s), words 2((i-1)&1), +1.
 template <class GA>
 __device__ __forceinline__ int source_walk(const RoundKeys &rk, const GA &G,
-                                           uint32_t s, int32_t p_s, uint32_t deg_s,
+                                           uint32_t s, int32_t b_s, uint32_t deg_s,
                                            int32_t r, int len, int32_t *out) {
-  int32_t p = p_s;
+  int32_t b = b_s;
   uint32_t deg = deg_s;
   uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
   for (int i = 1; i <= len; ++i) {
     if (deg == 0) return i - 1;
     if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
-    const auto e = adj_entry(G, p, deg, (i & 1) ? x0 : x2, (i & 1) ? x1 : x3);
-    p = entry_pos(G, e);
-    out[i - 1] = p;
-    deg = entry_deg(G, e, p);
+    const auto e = adj_entry(G, b, deg, (i & 1) ? x0 : x2, (i & 1) ? x1 : x3);
+    const int32_t x = entry_pos(G, e);
+    out[i - 1] = x;
+    b = entry_next(G, e, x, deg);
   }
   return len;
 }
@@ -265,18 +293,18 @@ struct PairSet {
   uint32_t s;          // source id (Philox counter word 3)
 };
 
-// All pairs of target u (position beg_u, degree deg_u > 0) walked by one
+// All pairs of target u (list base b_u, degree deg_u > 0) walked by one
 // warp with lane refill; per-lane totals of meetings c, weight W and steps st
 // are added to the arguments (not reduced across the warp).
 template <class GA>
 __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
                                             const PairSet &S, uint32_t u,
-                                            int32_t beg_u, uint32_t deg_u,
+                                            int32_t b_u, uint32_t deg_u,
                                             uint32_t lanes_below, uint32_t &c,
                                             unsigned long long &W, uint32_t &st) {
   int32_t next = 0;  // first unassigned pair (warp-uniform)
   bool live = false;
-  int32_t a = 0, i = 1, p = 0;
+  int32_t a = 0, i = 1, b = 0;
   uint32_t deg = 0, j = 0;
   for (;;) {
     const uint32_t idle = __ballot_sync(0xffffffffu, !live);
@@ -287,7 +315,7 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
           live = true;
           j = (uint32_t)S.pair_j[a];
           i = 1;
-          p = beg_u;
+          b = b_u;
           deg = deg_u;
         }
       }
@@ -298,7 +326,7 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
       uint32_t x0, x1, x2, x3;
       philox(rk, (uint32_t)(i - 1) >> 1, j, u, S.s, x0, x1, x2, x3);
       // odd step i
-      auto e = adj_entry(G, p, deg, x0, x1);
+      auto e = adj_entry(G, b, deg, x0, x1);
       int32_t x = entry_pos(G, e);
       ++st;
       if (x == S.Hc[S.R[i] + a]) {
@@ -308,12 +336,12 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
       } else if (a >= S.cnt[i + 1]) {
         live = false;  // cap reached
       } else {
-        deg = entry_deg(G, e, x);
+        b = entry_next(G, e, x, deg);
         if (deg == 0) {
           live = false;  // no in-neighbours: the walk ends
         } else {
           // even step i+1
-          e = adj_entry(G, x, deg, x2, x3);
+          e = adj_entry(G, b, deg, x2, x3);
           x = entry_pos(G, e);
           ++st;
           if (x == S.Hc[S.R[i + 1] + a]) {
@@ -323,9 +351,8 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
           } else if (a >= S.cnt[i + 2]) {
             live = false;
           } else {
-            deg = entry_deg(G, e, x);
+            b = entry_next(G, e, x, deg);
             if (deg == 0) live = false;
-            p = x;
             i += 2;
           }
         }
@@ -432,11 +459,11 @@ template <class GA>
 __device__ __forceinline__ void walk_target_literal(
     const RoundKeys &rk, const GA &G, const PairSet &S, const FeistelShape &f,
     const int32_t *P, int L, const double *aw, uint32_t u,
-    int32_t beg_u, uint32_t deg_u, uint32_t lanes_below, uint32_t &c,
+    int32_t b_u, uint32_t deg_u, uint32_t lanes_below, uint32_t &c,
     unsigned long long &W, uint32_t &st) {
   int32_t next = 0;
   bool live = false;
-  int32_t a = 0, i = 1, p = 0, l2 = 0;
+  int32_t a = 0, i = 1, b = 0, l2 = 0;
   uint32_t deg = 0, t = 0;
   // The target walks of pairs [base, base + 64), computed by the whole warp
   // (lane k: pair base + k in tw0, base + 32 + k in tw1) so that no lane
@@ -471,7 +498,7 @@ __device__ __forceinline__ void walk_target_literal(
         l2 = (int32_t)(g >> 24);
         live = l2 >= 1;  // a length-0 target walk takes no step
         i = 1;
-        p = beg_u;
+        b = b_u;
         deg = deg_u;
       }
       next += __popc(idle);
@@ -480,7 +507,7 @@ __device__ __forceinline__ void walk_target_literal(
     if (live) {
       uint32_t x0, x1, x2, x3;
       philox(rk, (uint32_t)(i - 1) >> 1, t, u, S.s, x0, x1, x2, x3);
-      auto e = adj_entry(G, p, deg, x0, x1);
+      auto e = adj_entry(G, b, deg, x0, x1);
       int32_t x = entry_pos(G, e);
       ++st;
       if (x == S.Hc[S.R[i] + a]) {
@@ -490,11 +517,11 @@ __device__ __forceinline__ void walk_target_literal(
       } else if (a >= S.cnt[i + 1] || i >= l2) {
         live = false;
       } else {
-        deg = entry_deg(G, e, x);
+        b = entry_next(G, e, x, deg);
         if (deg == 0) {
           live = false;
         } else {
-          e = adj_entry(G, x, deg, x2, x3);
+          e = adj_entry(G, b, deg, x2, x3);
           x = entry_pos(G, e);
           ++st;
           if (x == S.Hc[S.R[i + 1] + a]) {
@@ -504,9 +531,8 @@ __device__ __forceinline__ void walk_target_literal(
           } else if (a >= S.cnt[i + 2] || i + 1 >= l2) {
             live = false;
           } else {
-            deg = entry_deg(G, e, x);
+            b = entry_next(G, e, x, deg);
             if (deg == 0) live = false;
-            p = x;
             i += 2;
           }
         }

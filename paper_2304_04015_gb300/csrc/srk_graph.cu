@@ -4,8 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "srk_internal.h"
 
@@ -181,36 +183,101 @@ __global__ void k_validate_csr(const int32_t *__restrict__ row_ptr,
   }
 }
 
-// Packed adjacency (layout in srk_internal.h): node v's in-degree followed by
-// its in-neighbours' (degree code, position) entries, in the CSR's list
-// order, at pos(v) = v + row_ptr[v].  A walk step reads one entry, which
-// names the next node and usually its degree too, instead of a row_ptr pair
-// and a col entry.
-__global__ void k_build_adj_heads(const int32_t *__restrict__ row_ptr, int32_t n,
-                                  uint32_t *__restrict__ adj) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-    adj[v + row_ptr[v]] = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+// Packed adjacency with 4-byte entries (layout in srk_internal.h).  A walk
+// step reads one entry, which names the next node and, unless that node is a
+// hub, its degree too, instead of a row_ptr pair and a col entry.
+
+// Last v with row_ptr[v] <= e: the owner of edge e.
+__device__ __forceinline__ int32_t edge_owner(const int32_t *row_ptr, int32_t n, int64_t e) {
+  int32_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int32_t mid = lo + (hi - lo + 1) / 2;
+    if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
-// Edge e of list v (row_ptr[v] <= e < row_ptr[v+1]) lands at
-// pos(v) + 1 + (e - row_ptr[v]) = v + 1 + e.
-__global__ void k_build_adj_lists(const int32_t *__restrict__ row_ptr,
-                                  const int32_t *__restrict__ col, int32_t n,
-                                  int64_t m, int pos_bits,
-                                  uint32_t *__restrict__ adj) {
+// flag[v] = 1 for a hub (in-degree dmax or more).
+__global__ void k_hub_flags(const int32_t *__restrict__ row_ptr, int32_t n, uint32_t dmax,
+                            int32_t *__restrict__ flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    flag[v] = (uint32_t)(row_ptr[v + 1] - row_ptr[v]) >= dmax ? 1 : 0;
+}
+
+// Landing heat of hub y (index hidx[y] among the hubs): the sum, over the
+// lists I(v) that hold y, of floor((2^32 - 1) / |I(v)|), i.e. the expected
+// number of one-step walks from all nodes that land on y, in fixed point.
+// The additions are integer, so their order does not change the result.
+__global__ void k_hub_heat(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                           int32_t n, int64_t m, uint32_t dmax, const int32_t *__restrict__ hidx,
+                           unsigned long long *__restrict__ heat) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int32_t y = col[e];
+    if ((uint32_t)(row_ptr[y + 1] - row_ptr[y]) < dmax) continue;
+    const int32_t v = edge_owner(row_ptr, n, e);
+    const uint32_t dv = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+    atomicAdd(&heat[hidx[y]], (unsigned long long)(0xFFFFFFFFu / dv));
+  }
+}
+
+__global__ void k_hub_deg(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ ids,
+                          int32_t H, int32_t *__restrict__ deg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < H; h += stride)
+    deg[h] = row_ptr[ids[h] + 1] - row_ptr[ids[h]];
+}
+
+// Words a node takes after the hub region: 1 + |I(v)|, or 0 for a hub.
+__global__ void k_nonhub_words(const int32_t *__restrict__ row_ptr, int32_t n, uint32_t dmax,
+                               int32_t *__restrict__ words) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const uint32_t d = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+    words[v] = d >= dmax ? 0 : (int32_t)(1 + d);
+  }
+}
+
+// Positions and headers of the nodes that are not hubs: 2H + their words'
+// exclusive prefix `off`, in id order.
+__global__ void k_narrow_pos(const int32_t *__restrict__ row_ptr, int32_t n, uint32_t dmax,
+                             int32_t H, const int32_t *__restrict__ off,
+                             int32_t *__restrict__ npos, uint32_t *__restrict__ adj) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const uint32_t d = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+    if (d >= dmax) continue;
+    const int32_t p = 2 * H + off[v];
+    npos[v] = p;
+    adj[p] = d;
+  }
+}
+
+// The hub of rank r sits at position 2r.
+__global__ void k_hub_pos(const int32_t *__restrict__ rank_ids, int32_t H,
+                          int32_t *__restrict__ npos) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < H; r += stride)
+    npos[rank_ids[r]] = (int32_t)(2 * r);
+}
+
+// Edge e of list v lands at base(v) + (e - row_ptr[v]), base(v) = npos[v] + 1
+// or, for a hub, the list offset in its header.
+__global__ void k_narrow_lists(const int32_t *__restrict__ row_ptr,
+                               const int32_t *__restrict__ col, int32_t n, int64_t m,
+                               int pos_bits, const int32_t *__restrict__ npos,
+                               uint32_t *__restrict__ adj) {
   const uint32_t dmax = (uint32_t)((1ull << (32 - pos_bits)) - 1ull);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    int32_t lo = 0, hi = n - 1;  // last v with row_ptr[v] <= e
-    while (lo < hi) {
-      const int32_t mid = lo + (hi - lo + 1) / 2;
-      if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
-    }
+    const int32_t v = edge_owner(row_ptr, n, e);
+    const uint32_t dv = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
+    const int64_t base = dv < dmax ? (int64_t)npos[v] + 1 : (int64_t)adj[npos[v] + 1];
     const int32_t y = col[e];
     const uint32_t dy = (uint32_t)(row_ptr[y + 1] - row_ptr[y]);
     const uint32_t code = dy < dmax ? dy : dmax;
-    adj[(int64_t)lo + 1 + e] = (code << pos_bits) | (uint32_t)(y + row_ptr[y]);
+    adj[base + (e - row_ptr[v])] = (code << pos_bits) | (uint32_t)npos[y];
   }
 }
 
@@ -228,11 +295,7 @@ __global__ void k_build_adjw_lists(const int32_t *__restrict__ row_ptr,
                                    uint2 *__restrict__ adj2) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    int32_t lo = 0, hi = n - 1;  // last v with row_ptr[v] <= e
-    while (lo < hi) {
-      const int32_t mid = lo + (hi - lo + 1) / 2;
-      if ((int64_t)row_ptr[mid] <= e) lo = mid; else hi = mid - 1;
-    }
+    const int32_t lo = edge_owner(row_ptr, n, e);
     const int32_t y = col[e];
     adj2[(int64_t)lo + 1 + e] =
         make_uint2((uint32_t)(y + row_ptr[y]), (uint32_t)(row_ptr[y + 1] - row_ptr[y]));
@@ -284,11 +347,141 @@ extern "C" int srk_graph_free(srk_graph *g) {
     if (g->own_col) cudaFree(g->own_col);
     if (g->own_w) cudaFree(g->own_w);
     if (g->adj) cudaFree(g->adj);
+    if (g->npos) cudaFree(g->npos);
     if (g->act) cudaFree(g->act);
     free_lin_topo(g);
   }
   delete g;
   return rc;
+}
+
+// Smallest b with 2^b >= x (x >= 1), at most 31.
+static int bits_for(int64_t x) {
+  int b = 1;
+  while (b < 31 && ((int64_t)1 << b) < x) ++b;
+  return b;
+}
+
+// Builds the 4-byte-entry adjacency of g (sets adj, npos, n_hubs, pos_bits).
+// The hub count H and the position width pb depend on each other (a hub has
+// degree 2^(32-pb) - 1 or more, and positions run to n + m + H): pb grows
+// from ceil(log2(n + m)) until it holds.  Hubs are ranked by landing heat,
+// ties by id, so the layout is a function of the graph alone.
+static int build_narrow(srk_graph *g, int dev) {
+  const int32_t n = g->n;
+  const int64_t m = g->m;
+  const int blocks = sm_count(dev) * 4;
+  int32_t *flag = nullptr, *off = nullptr, *ids = nullptr, *hdeg = nullptr;
+  unsigned long long *heat = nullptr;
+  auto cleanup = [&]() {
+    if (flag) cudaFree(flag);
+    if (off) cudaFree(off);
+    if (ids) cudaFree(ids);
+    if (hdeg) cudaFree(hdeg);
+    if (heat) cudaFree(heat);
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&flag, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+      (e = cudaMalloc(&off, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "srk_graph_load: hub flags");
+  }
+  int pb = bits_for((int64_t)n + m);
+  int32_t H = 0;
+  for (int it = 0;; ++it) {
+    const uint32_t dmax = (uint32_t)((1ull << (32 - pb)) - 1ull);
+    k_hub_flags<<<blocks, 256>>>(g->row_ptr, n, dmax, flag);
+    k_scan<<<1, 1024>>>(flag, off, n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&H, off + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "srk_graph_load: counting hubs");
+    }
+    const int64_t total = (int64_t)n + m + H;
+    if (total > INT32_MAX || it >= 32) {
+      cleanup();
+      return fail(SRK_EINVAL, "graph too large for 4-byte adjacency entries (n + m + hubs = %lld)",
+                  (long long)total);
+    }
+    const int pb2 = bits_for(total);
+    if (pb2 <= pb) break;
+    pb = pb2;
+  }
+  const uint32_t dmax = (uint32_t)((1ull << (32 - pb)) - 1ull);
+  const size_t words = (size_t)n + (size_t)m + (size_t)H;
+  std::vector<int32_t> rank_ids((size_t)H);
+  std::vector<uint32_t> head(2 * (size_t)H);
+  if (H > 0) {
+    if ((e = cudaMalloc(&ids, sizeof(int32_t) * (size_t)H)) != cudaSuccess ||
+        (e = cudaMalloc(&hdeg, sizeof(int32_t) * (size_t)H)) != cudaSuccess ||
+        (e = cudaMalloc(&heat, sizeof(unsigned long long) * (size_t)H)) != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "srk_graph_load: hub arrays");
+    }
+    cudaMemset(heat, 0, sizeof(unsigned long long) * (size_t)H);
+    k_active_scatter<<<blocks, 256>>>(flag, off, n, ids);  // hubs in id order
+    k_hub_deg<<<blocks, 256>>>(g->row_ptr, ids, H, hdeg);
+    if (m > 0)
+      k_hub_heat<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, dmax, off, heat);
+    std::vector<int32_t> h_ids((size_t)H), h_deg((size_t)H);
+    std::vector<unsigned long long> h_heat((size_t)H);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h_ids.data(), ids, sizeof(int32_t) * (size_t)H, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h_deg.data(), hdeg, sizeof(int32_t) * (size_t)H, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h_heat.data(), heat, sizeof(unsigned long long) * (size_t)H,
+                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "srk_graph_load: hub heat");
+    }
+    std::vector<int32_t> order((size_t)H);
+    for (int32_t h = 0; h < H; ++h) order[(size_t)h] = h;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      return h_heat[(size_t)x] > h_heat[(size_t)y];
+    });
+    int64_t hub_entries = 0;
+    for (int32_t h = 0; h < H; ++h) hub_entries += h_deg[(size_t)h];
+    // hub lists follow the hub region and the other nodes' words
+    int64_t at = 2 * (int64_t)H + ((int64_t)n - H) + (m - hub_entries);
+    for (int32_t r = 0; r < H; ++r) {
+      const int32_t h = order[(size_t)r];
+      rank_ids[(size_t)r] = h_ids[(size_t)h];
+      head[2 * (size_t)r] = (uint32_t)h_deg[(size_t)h];
+      head[2 * (size_t)r + 1] = (uint32_t)at;
+      at += h_deg[(size_t)h];
+    }
+  }
+  if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) * (words > 0 ? words : 1))) != cudaSuccess ||
+      (e = cudaMalloc(&g->npos, sizeof(int32_t) * (size_t)n)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "srk_graph_load: packed adjacency");
+  }
+  if (H > 0) {
+    e = cudaMemcpy(g->adj, head.data(), sizeof(uint32_t) * 2 * (size_t)H, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ids, rank_ids.data(), sizeof(int32_t) * (size_t)H, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(e, "srk_graph_load: hub headers");
+    }
+    k_hub_pos<<<blocks, 256>>>(ids, H, g->npos);
+  }
+  k_nonhub_words<<<blocks, 256>>>(g->row_ptr, n, dmax, flag);
+  k_scan<<<1, 1024>>>(flag, off, n);
+  k_narrow_pos<<<blocks, 256>>>(g->row_ptr, n, dmax, H, off, g->npos, g->adj);
+  if (m > 0)
+    k_narrow_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, pb, g->npos, g->adj);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "srk_graph_load: building the packed adjacency");
+  g->pos_bits = pb;
+  g->n_hubs = H;
+  return SRK_OK;
 }
 
 extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
@@ -376,42 +569,34 @@ extern "C" int srk_graph_load(const int32_t *row_ptr, const int32_t *col,
     }
   }
   {
-    int pb = 1;
-    while (pb < 31 && ((int64_t)1 << pb) < (int64_t)n + m) ++pb;  // positions < n + m
+    const int pb = bits_for((int64_t)n + m);  // positions < n + m (wide layout)
     g->pos_bits = pb;
-    // Layout by size (measured on R-MAT graphs): 32-bit entries while their
-    // degree code reaches 63 (positions of at most 26 bits; the headers read
-    // for larger nodes are few and cached, and the graph or most of it stays
-    // in L2); at 27 bits the plain CSR (row_ptr, 4 B per node, stays in L2
-    // while the col reads go to DRAM); beyond, 64-bit entries: a code of 15
-    // or less would send most steps to a second, uncached read.
+    // Layout by size (measured on R-MAT graphs 20-24): 4-byte entries up to
+    // 28 position bits (degree codes down to 15; the hubs' headers, packed
+    // at the front in landing order, stay cached while the entries are half
+    // the size of 8-byte ones); beyond, 8-byte entries, which need no header
+    // read.  The CSR layout is only taken when asked for.
     g->layout = (flags & SRK_ADJ_WIDE)     ? 1
                 : (flags & SRK_ADJ_CSR)    ? 2
                 : (flags & SRK_ADJ_NARROW) ? 0
-                : pb <= 26                 ? 0
-                : pb == 27                 ? 2
+                : pb <= 28                 ? 0
                                            : 1;
-    const size_t words = g->layout == 2 ? 1 : ((size_t)n + (size_t)m) * (g->layout == 1 ? 2 : 1);
-    if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) * words)) != cudaSuccess) {
-      int rc = cuda_fail(e, "srk_graph_load: packed adjacency");
-      srk_graph_free(g);
-      return rc;
-    }
-    if (g->layout == 2) {
-      // the walks read row_ptr and col directly
+    int rc = SRK_OK;
+    if (g->layout == 0) {
+      rc = build_narrow(g, dev);
+    } else if ((e = cudaMalloc(&g->adj, sizeof(uint32_t) *
+                                            (g->layout == 2 ? 1 : 2 * ((size_t)n + (size_t)m)))) !=
+               cudaSuccess) {
+      rc = cuda_fail(e, "srk_graph_load: packed adjacency");
     } else if (g->layout == 1) {
       uint2 *adj2 = reinterpret_cast<uint2 *>(g->adj);
       k_build_adjw_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, adj2);
       if (m > 0) k_build_adjw_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, adj2);
-    } else {
-      k_build_adj_heads<<<sm_count(dev) * 4, 256>>>(g->row_ptr, n, g->adj);
-      if (m > 0)
-        k_build_adj_lists<<<sm_count(dev) * 8, 256>>>(g->row_ptr, g->col, n, m, pb, g->adj);
-    }
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-      int rc = cuda_fail(e, "srk_graph_load: building the packed adjacency");
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) rc = cuda_fail(e, "srk_graph_load: building the packed adjacency");
+    }  // CSR: the walks read row_ptr and col directly
+    if (rc != SRK_OK) {
       srk_graph_free(g);
       return rc;
     }

@@ -12,21 +12,26 @@ struct srk_graph {
   const int32_t *row_ptr = nullptr;  // device, n+1
   const int32_t *col = nullptr;      // device, m
   const float *edge_w = nullptr;     // device, m or null
-  // Packed adjacency (owned, n + m words): node v occupies the words
-  // pos(v) = v + row_ptr[v] .. pos(v) + |I(v)|.  adj[pos(v)] = |I(v)|; entry
-  // k of the list, adj[pos(v) + 1 + k], holds the k-th in-neighbour y as
-  // (min(|I(y)|, deg_max) << pos_bits) | pos(y), deg_max = 2^(32-pos_bits) - 1,
+  // Packed adjacency (owned, n + m + H words, H the hubs below).  Node v's
+  // identity inside the walk kernels is its position npos[v].  A node of
+  // in-degree d < deg_max = 2^(32-pos_bits) - 1 has the word d at its
+  // position and its list right after it; a hub (d >= deg_max) has two words
+  // {d, offset of its list} at position 2r of the hub region at the front,
+  // r its rank by how often walks land on it (so the hot headers share
+  // sectors), and its list after the other nodes'.  Entry k of v's list holds
+  // the k-th in-neighbour y as (min(|I(y)|, deg_max) << pos_bits) | npos[y],
   // so a walk step learns the next node's degree from the entry it reads and
-  // reads the header only when the degree is deg_max or more.  A node's
-  // position is its identity inside the walk kernels.
+  // reads a header only at a hub.
   // Wide layout (layout = 1, chosen when positions need more than 27 bits
   // or forced by SRK_ADJ_WIDE): 2 (n + m) words forming 8-byte entries at
-  // the same positions, adj[pos(v)] = {0, |I(v)|} and entries
+  // positions v + row_ptr[v], adj[pos(v)] = {0, |I(v)|} and entries
   // {pos(y), |I(y)|}, so a step never reads a header.  CSR layout (layout =
   // 2, at 27 bits or forced by SRK_ADJ_CSR): no packed copy; nodes are their
   // ids and a step reads row_ptr and col.
   uint32_t *adj = nullptr;
-  int32_t pos_bits = 1;  // positions < 2^pos_bits
+  int32_t *npos = nullptr;  // narrow layout: positions, n (owned)
+  int32_t n_hubs = 0;       // narrow layout: H
+  int32_t pos_bits = 1;     // positions < 2^pos_bits
   int layout = 0;        // 0 narrow, 1 wide, 2 CSR (no packed adjacency; walks read row_ptr/col)
   // Nodes with at least one in-neighbour, ascending (owned): the only targets
   // whose score can be nonzero.

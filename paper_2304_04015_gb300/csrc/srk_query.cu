@@ -35,7 +35,7 @@ namespace srk {
 template <int kLayout>
 __global__ void __launch_bounds__(256)
 k_source_walks(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-               const uint32_t *__restrict__ adj, int pos_bits,
+               const uint32_t *__restrict__ adj, const int32_t *__restrict__ npos, int pos_bits,
                const __grid_constant__ QueryTab tab,
                int32_t *__restrict__ spos, int32_t *__restrict__ seff,
                int32_t *__restrict__ kdraw, int32_t *__restrict__ grp_cnt,
@@ -46,16 +46,16 @@ k_source_walks(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ 
   const RoundKeys rk = round_keys(tab.key0, tab.key1);
   const int Ls = tab.L > 0 ? tab.L : 1;
   const uint32_t s = (uint32_t)tab.s;
-  const auto G = adj_view<kLayout>(adj, pos_bits, row_ptr, col);
-  const int32_t p_s = node_pos(G, row_ptr, tab.s);  // s inside the kernels
-  const uint32_t deg_s = header_deg(G, p_s);
+  const auto G = adj_view<kLayout>(adj, npos, pos_bits, row_ptr, col);
+  uint32_t deg_s = 0;
+  const int32_t b_s = node_start(G, row_ptr, tab.s, deg_s);
   unsigned long long steps = 0;
   for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < tab.N_tot;
        r += gridDim.x * blockDim.x) {
     grp_cnt[r] = 0;
     kdraw[r] = (r >= 1) ? fy_draw(rk, s, r) : 0;
     const int len = stratum_of(P, tab.L, r);
-    const int eff = source_walk(rk, G, s, p_s, deg_s, r, len, spos + (int64_t)r * Ls);
+    const int eff = source_walk(rk, G, s, b_s, deg_s, r, len, spos + (int64_t)r * Ls);
     seff[r] = eff;
     steps += (unsigned long long)eff;
   }
@@ -271,9 +271,10 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
 // to W_u.  The warp then reduces and writes count, W and s~(s,u) = W 2^-32 / z
 // (s~(s,s) = 1).
 struct TargetArgs {
-  const int32_t *row_ptr;  // start positions of the targets: u + row_ptr[u]
+  const int32_t *row_ptr;  // CSR offsets (wide and CSR layouts locate nodes by them)
   const int32_t *col;      // in-neighbour lists (CSR layout)
   const uint32_t *adj;     // packed adjacency (see srk_internal.h)
+  const int32_t *npos;     // 4-byte-entry layout: node positions
   int32_t pos_bits;
   int32_t n, s, L;
   uint32_t key0, key1;
@@ -320,7 +321,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31;
   const uint32_t lanes_below = (1u << lane) - 1u;
-  const auto G = adj_view<kLayout>(A.adj, A.pos_bits, A.row_ptr, A.col);
+  const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   PairSet S;
   S.cnt = cnt;
   S.R = R;
@@ -349,14 +350,14 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
     if (u < 0) break;
     uint32_t c = 0, st = 0;
     unsigned long long W = 0;
-    const int32_t beg_u = node_pos(G, A.row_ptr, u);  // u inside the kernels
-    const uint32_t deg_u = header_deg(G, beg_u);
+    uint32_t deg_u = 0;
+    const int32_t b_u = node_start(G, A.row_ptr, u, deg_u);
     if (u != A.s && deg_u > 0) {
       if (kLiteral)
-        walk_target_literal(rk, G, S, fs, Psh, A.L, X.a, (uint32_t)u, beg_u, deg_u,
+        walk_target_literal(rk, G, S, fs, Psh, A.L, X.a, (uint32_t)u, b_u, deg_u,
                             lanes_below, c, W, st);
       else
-        walk_target(rk, G, S, (uint32_t)u, beg_u, deg_u, lanes_below, c, W, st);
+        walk_target(rk, G, S, (uint32_t)u, b_u, deg_u, lanes_below, c, W, st);
     }
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
@@ -437,13 +438,13 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   cudaError_t e = cudaMemsetAsync(w.small, 0, kSmallBytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "clearing query counters");
   if (g->layout == kWide)
-    k_source_walks<kWide><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->pos_bits, t,
+    k_source_walks<kWide><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->npos, g->pos_bits, t,
                                               w.spos, w.seff, w.kdraw, w.grp_cnt, w.small);
   else if (g->layout == kCsr)
-    k_source_walks<kCsr><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->pos_bits, t,
+    k_source_walks<kCsr><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->npos, g->pos_bits, t,
                                              w.spos, w.seff, w.kdraw, w.grp_cnt, w.small);
   else
-    k_source_walks<kNarrow><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->pos_bits, t,
+    k_source_walks<kNarrow><<<gN, 256, 0, st>>>(g->row_ptr, g->col, g->adj, g->npos, g->pos_bits, t,
                                                 w.spos, w.seff, w.kdraw, w.grp_cnt, w.small);
   k_fy_rank<<<gN, 256, 0, st>>>(w.kdraw, w.grp_cnt, w.rank, N);
   k_scan<<<1, 1024, 0, st>>>(w.grp_cnt, w.grp_off, N);
@@ -467,6 +468,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.row_ptr = g->row_ptr;
   A.col = g->col;
   A.adj = g->adj;
+  A.npos = g->npos;
   A.pos_bits = g->pos_bits;
   A.n = g->n;
   A.s = t.s;

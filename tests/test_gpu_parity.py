@@ -35,6 +35,27 @@ def rmat_graph(scale, seed=1):
     return rmat_in_csr(scale, seed=seed)
 
 
+@functools.lru_cache(maxsize=None)
+def hub_graph():
+    """20,000 nodes, 40 of them hubs with ~9,000 in-neighbours each; every
+    node also has two hubs among its in-neighbours, so most walk steps land
+    on a hub."""
+    from srk_inputs import csr_from_edges
+    rng = np.random.default_rng(5)
+    n = 20000
+    hubs = rng.choice(n, size=40, replace=False)
+    src, dst = [], []
+    for h in hubs:
+        src.append(rng.choice(n, size=9000, replace=False))
+        dst.append(np.full(9000, h))
+    d = rng.poisson(4.0, size=n)
+    dst.append(np.repeat(np.arange(n), d))
+    src.append(rng.integers(0, n, size=int(d.sum())))
+    dst.append(np.repeat(np.arange(n), 2))
+    src.append(hubs[rng.integers(0, 40, size=2 * n)])
+    return csr_from_edges(n, np.concatenate(src), np.concatenate(dst))
+
+
 def gpu_query(srk, rp, col, s, eps, seed, device_outputs=True, **kw):
     import torch
     dev = torch.device("cuda:0")
@@ -495,6 +516,44 @@ def test_wide_adjacency_layout_bit_exact(srk):
         g.close()
     ref = oracle_query(rp, col, 17, 0.1, 2, **TINY)
     assert np.array_equal(counts, ref.count) and np.array_equal(scores, ref.scores)
+
+
+def test_hub_headers_bit_exact(srk):
+    # With 4-byte entries the degree code holds degrees below 2^(32-b) - 1,
+    # 2^b >= n + m + H (here b = 19: 8,191); the 40 hubs keep theirs in the
+    # header region.  A hub source, a hub target and landings on hubs all go
+    # through it; the other layouts and the batched path must agree.
+    import torch
+    rp, col = hub_graph()
+    n, m = rp.size - 1, col.size
+    deg = np.diff(rp)
+    hubs = np.flatnonzero(deg >= 8191)
+    assert hubs.size == 40 and deg[deg < 8191].max() < 100
+    assert 2 ** 18 < n + m + 40 <= 2 ** 19
+    plain = int(np.flatnonzero((deg > 0) & (deg < 8191))[7])
+    for s, seed in ((int(hubs[3]), 3), (plain, 4)):
+        gpu = gpu_query(srk, rp, col, s, 0.1, seed, **TINY)
+        assert_parity(gpu, oracle_query(rp, col, s, 0.1, seed, **TINY))
+        assert gpu[1][hubs].sum() > 0
+    dev = torch.device("cuda:0")
+    rows = {}
+    for layout in ("narrow", "wide", "csr"):
+        g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                               layout=layout)
+        try:
+            out = torch.empty((2, n), dtype=torch.float64, device=dev)
+            cnt = torch.empty((2, n), dtype=torch.int32, device=dev)
+            srk.srk_multi_source(g, [int(hubs[3]), plain], C, [0.1, 0.1], 3, out, cnt, **TINY)
+            one = torch.empty(n, dtype=torch.float64, device=dev)
+            srk.srk_single_source(g, plain, C, 0.1, 3, one, **TINY)
+            torch.cuda.synchronize()
+            assert torch.equal(one, out[1])
+            rows[layout] = (out.cpu().numpy(), cnt.cpu().numpy())
+        finally:
+            g.close()
+    for layout in ("wide", "csr"):
+        assert np.array_equal(rows[layout][0], rows["narrow"][0])
+        assert np.array_equal(rows[layout][1], rows["narrow"][1])
 
 
 def test_degenerate_graphs_and_calls(srk):
