@@ -21,8 +21,11 @@
 // one thread (up to 4 entries), a group of 8 lanes (up to 32), a warp (up to
 // 512), or warps over chunks of 512 entries whose partial sums are added in
 // chunk order by the warp that finishes the list's last chunk, so no result
-// depends on timing.  The vectors are stored node-major, n x (L+1), so the
-// per-edge gradient pass reads each node's L values together.
+// depends on timing.  The vectors are stored term-major, (L+1) x n: a gather
+// reads one contiguous term, whose most referenced entries (R-MAT's low ids)
+// share sectors and stay in L1.  The per-edge gradient pass reads node-major
+// copies of h and yb (one transpose each), so each source node's L values
+// come together.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -79,8 +82,8 @@ struct srk_linear_ctx {
   float *Pe = nullptr;      // m: w_e / W_a, in-list order
   float *PeT = nullptr;     // m: the same values in out-list order
   float *Wa = nullptr;      // n: in-weight sums
-  float *y = nullptr;       // n x (L+1), node-major: y[a (L+1) + t] = (P^t e_s)[a]
-  float *h = nullptr;       // n x (L+1), node-major partial sums, h_0 = s_vec
+  float *y = nullptr;       // (L+1) x n, term-major: y[t n + a] = (P^t e_s)[a]
+  float *h = nullptr;       // (L+1) x n, term-major partial sums, h_0 = s_vec
   double *part = nullptr;   // partial sums of the chunk items (either direction)
   int32_t *done = nullptr;  // finished chunks per long list (zero between uses)
   int *bad = nullptr;       // weight check flag
@@ -125,14 +128,11 @@ __device__ __forceinline__ T list_partial(const V &val, int64_t b, int64_t e, in
 }
 
 // Entry values and result writers of the segmented reductions.
-struct GatherVal {  // w[k] in[idx[k]], in a column of stride S
+struct GatherVal {  // w[k] in[idx[k]]
   const int32_t *idx;
   const float *w;
   const float *in;
-  int32_t S;
-  __device__ __forceinline__ float operator()(int64_t k) const {
-    return w[k] * in[(int64_t)idx[k] * S];
-  }
+  __device__ __forceinline__ float operator()(int64_t k) const { return w[k] * in[idx[k]]; }
 };
 struct DotVal {  // x[k] w[k]
   const float *x;
@@ -143,14 +143,12 @@ struct WeightVal {  // w[k]
   const float *w;
   __device__ __forceinline__ float operator()(int64_t k) const { return w[k]; }
 };
-struct WriteAxpy {  // out[a] = alpha add[a] + beta sum (columns of stride S; add may be null)
+struct WriteAxpy {  // out[a] = alpha add[a] + beta sum (add may be null)
   float *out;
   const float *add;
   float alpha, beta;
-  int32_t S;
   __device__ __forceinline__ void operator()(int32_t a, float sum) const {
-    const int64_t i = (int64_t)a * S;
-    out[i] = (add ? alpha * add[i] : 0.0f) + beta * sum;
+    out[a] = (add ? alpha * add[a] : 0.0f) + beta * sum;
   }
 };
 struct WriteVec {  // out[a] = sum
@@ -393,33 +391,54 @@ __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__res
     dst[k] = src[idx[k]];
 }
 
-// v[a] = (a == s) for a node-major vector column (stride S).
-__global__ void k_lin_unit(float *__restrict__ v, int32_t S, int32_t n, int32_t s) {
+// v[a] = (a == s).
+__global__ void k_lin_unit(float *__restrict__ v, int32_t n, int32_t s) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    v[i * S] = (i == s) ? 1.0f : 0.0f;
+    v[i] = (i == s) ? 1.0f : 0.0f;
 }
 
-// out[a] = d in[a] (columns of stride S).
-__global__ void k_lin_scale(const float *__restrict__ in, float d, int32_t S, int32_t n,
+// out[a] = d in[a].
+__global__ void k_lin_scale(const float *__restrict__ in, float d, int32_t n,
                             float *__restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[i * S] = d * in[i * S];
+    out[i] = d * in[i];
 }
 
-// G_e for every edge e = (u -> a), edge-parallel: consecutive edges mostly
-// share a, whose rows of gb and y are then read once per warp.
+// Node-major copy of a term-major (S x n) matrix: block b moves nodes
+// [32 b, 32 b + 32) through shared memory (S x 33 floats), reading 32
+// consecutive nodes of a term and writing the 32 S consecutive outputs.
+__global__ void __launch_bounds__(256) k_lin_rows(const float *__restrict__ src, int32_t S,
+                                                  int32_t n, float *__restrict__ dst) {
+  extern __shared__ float tile[];
+  const int64_t a0 = (int64_t)blockIdx.x * 32;
+  const int na = (int)((int64_t)n - a0 < 32 ? (int64_t)n - a0 : 32);
+  for (int q = threadIdx.x; q < S * 32; q += blockDim.x) {
+    const int t = q >> 5, j = q & 31;
+    if (j < na) tile[t * 33 + j] = src[(int64_t)t * n + a0 + j];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < na * S; q += blockDim.x) {
+    const int j = q / S, t = q - j * S;
+    dst[(a0 + j) * S + t] = tile[t * 33 + j];
+  }
+}
+
+// G_e for every edge e = (u -> a), edge-parallel.  gb and y are term-major
+// (consecutive edges mostly share a, so a warp reads one word per term); h
+// and yb come as node-major rows hr, ybr (u is scattered, so a thread reads
+// u's L values from one row).
 __global__ void k_lin_edge_G(const int32_t *__restrict__ erow, const int32_t *__restrict__ col,
-                             int64_t m, const float *__restrict__ y,
-                             const float *__restrict__ h, const float *__restrict__ gb,
-                             const float *__restrict__ yb, int32_t L, float c,
+                             int64_t m, int32_t n, const float *__restrict__ y,
+                             const float *__restrict__ hr, const float *__restrict__ gb,
+                             const float *__restrict__ ybr, int32_t L, float c,
                              float *__restrict__ G) {
   const int32_t S = L + 1;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = erow[k], u = col[k];
-    const float *ga = gb + a * S, *ya = y + a * S, *hu = h + u * S, *ybu = yb + u * S;
+    const float *hu = hr + u * S, *ybu = ybr + u * S;
     float g = 0.0f;
     for (int t0 = 0; t0 < L; t0 += 4) {  // four terms' loads in flight
       float gv[4], yv[4], hv[4], bv[4];
@@ -427,8 +446,8 @@ __global__ void k_lin_edge_G(const int32_t *__restrict__ erow, const int32_t *__
       for (int j = 0; j < 4; ++j) {
         const int t = t0 + j;
         const bool ok = t < L;
-        gv[j] = ok ? ga[t] : 0.0f;
-        yv[j] = ok ? ya[t] : 0.0f;
+        gv[j] = ok ? gb[(int64_t)t * n + a] : 0.0f;
+        yv[j] = ok ? y[(int64_t)t * n + a] : 0.0f;
         hv[j] = ok ? hu[t + 1] : 0.0f;
         bv[j] = ok ? ybu[t + 1] : 0.0f;
       }
@@ -477,20 +496,18 @@ static void segmented(srk_linear_ctx *x, const int32_t *ptr, const Classes &C, V
                                               reinterpret_cast<T *>(x->part), x->done);
 }
 
-// out = alpha add + beta P^T in (columns of stride S; gather along in-lists).
+// out = alpha add + beta P^T in (n-vectors; gather along in-lists).
 static void gather_t(srk_linear_ctx *x, const float *in, const float *add, float alpha,
                      float beta, float *out, cudaStream_t st) {
-  const int32_t S = x->L + 1;
-  segmented<float>(x, x->g->row_ptr, x->topo->in, GatherVal{x->g->col, x->Pe, in, S},
-                   WriteAxpy{out, add, alpha, beta, S}, st);
+  segmented<float>(x, x->g->row_ptr, x->topo->in, GatherVal{x->g->col, x->Pe, in},
+                   WriteAxpy{out, add, alpha, beta}, st);
 }
 
-// out = scale P in (columns of stride S; gather along the transpose's out-lists).
+// out = scale P in (n-vectors; gather along the transpose's out-lists).
 static void gather_p(srk_linear_ctx *x, const float *in, float scale, float *out,
                      cudaStream_t st) {
-  const int32_t S = x->L + 1;
-  segmented<float>(x, x->topo->out_ptr, x->topo->out, GatherVal{x->topo->t_a, x->PeT, in, S},
-                   WriteAxpy{out, nullptr, 0.0f, scale, S}, st);
+  segmented<float>(x, x->topo->out_ptr, x->topo->out, GatherVal{x->topo->t_a, x->PeT, in},
+                   WriteAxpy{out, nullptr, 0.0f, scale}, st);
 }
 
 // Capacities of the class arrays of one direction.
@@ -733,14 +750,14 @@ extern "C" int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s
     k_lin_pe<<<gm, 256, 0, st>>>(edge_w, topo->erow, x->Wa, g->m, x->Pe, x->bad);
     k_gather_f32<<<gm, 256, 0, st>>>(x->Pe, topo->t_e, g->m, x->PeT);
   }
-  k_lin_unit<<<gn, 256, 0, st>>>(x->y, S, g->n, s);
-  for (int t = 1; t <= L; ++t) gather_p(x, x->y + (t - 1), 1.0f, x->y + t, st);  // y_t = P y_{t-1}
+  float *const y = x->y, *const h = x->h;
+  k_lin_unit<<<gn, 256, 0, st>>>(y, g->n, s);
+  for (int t = 1; t <= L; ++t) gather_p(x, y + (t - 1) * n, 1.0f, y + t * n, st);  // y_t = P y_{t-1}
   // h_L = D y_L, then h_t = D y_t + c P^T h_{t+1}
-  k_lin_scale<<<gn, 256, 0, st>>>(x->y + L, d, S, g->n, x->h + L);
-  for (int t = L - 1; t >= 0; --t) gather_t(x, x->h + (t + 1), x->y + t, d, fc, x->h + t, st);
-  // s_out = column 0 of h (stride S)
-  e = cudaMemcpy2DAsync(s_out, sizeof(float), x->h, sizeof(float) * S, sizeof(float), n,
-                        cudaMemcpyDeviceToDevice, st);
+  k_lin_scale<<<gn, 256, 0, st>>>(y + L * n, d, g->n, h + L * n);
+  for (int t = L - 1; t >= 0; --t) gather_t(x, h + (t + 1) * n, y + t * n, d, fc, h + t * n, st);
+  // s_out = h_0
+  e = cudaMemcpyAsync(s_out, h, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
   int hbad = 0;
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, x->bad, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -777,25 +794,31 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
   cudaMemPool_t mp = pool(dev);
   if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
   float *gb = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync((void **)&gb, sizeof(float) * (2 * vec + n), mp, st);
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&gb, sizeof(float) * (4 * vec + n), mp, st);
   if (e != cudaSuccess) return cuda_fail(e, "srk_linear_bwd: allocation");
-  float *yb = gb + vec, *T = gb + 2 * vec;
+  float *yb = gb + vec, *hr = gb + 2 * vec, *ybr = gb + 3 * vec, *T = gb + 4 * vec;
   const int gn = grid_of((int64_t)n, 256, dev), gm = grid_of(x->m, 256, dev);
   const float fc = (float)x->c, d = (float)(1.0 - x->c);
-  // gb column 0 = g (stride S)
-  cudaMemcpy2DAsync(gb, sizeof(float) * S, grad_s, sizeof(float), sizeof(float), n,
-                    cudaMemcpyDeviceToDevice, st);
-  for (int t = 1; t <= L; ++t) gather_p(x, gb + (t - 1), fc, gb + t, st);  // gb_t = c P gb_{t-1}
+  // gb_0 = g
+  cudaMemcpyAsync(gb, grad_s, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+  for (int t = 1; t <= L; ++t) gather_p(x, gb + (t - 1) * n, fc, gb + t * n, st);  // gb_t = c P gb_{t-1}
   if (L >= 1) {
-    // yb_L = D gb_L, yb_t = D gb_t + P^T yb_{t+1} for t = L-1 .. 1
-    k_lin_scale<<<gn, 256, 0, st>>>(gb + L, d, S, x->n, yb + L);
-    for (int t = L - 1; t >= 1; --t) gather_t(x, yb + (t + 1), gb + t, d, 1.0f, yb + t, st);
+    // yb_L = D gb_L, yb_t = D gb_t + P^T yb_{t+1} for t = L-1 .. 1 (yb_0 is not used)
+    cudaMemsetAsync(yb, 0, sizeof(float) * n, st);
+    k_lin_scale<<<gn, 256, 0, st>>>(gb + L * n, d, x->n, yb + L * n);
+    for (int t = L - 1; t >= 1; --t)
+      gather_t(x, yb + (t + 1) * n, gb + t * n, d, 1.0f, yb + t * n, st);
   }
   if (x->m > 0) {
     if (L >= 1) {
-      // G_e into grad_w, T_a = sum G_e P_e per in-list, then the normalisation
-      k_lin_edge_G<<<gm, 256, 0, st>>>(topo->erow, g->col, x->m, x->y, x->h, gb, yb, L, fc,
-                                       grad_w);
+      // node-major rows of h and yb, G_e into grad_w, T_a = sum G_e P_e per
+      // in-list, then the normalisation
+      const int gr = (int)((n + 31) / 32);
+      const size_t tile = sizeof(float) * 33 * (size_t)S;
+      k_lin_rows<<<gr, 256, tile, st>>>(x->h, S, x->n, hr);
+      k_lin_rows<<<gr, 256, tile, st>>>(yb, S, x->n, ybr);
+      k_lin_edge_G<<<gm, 256, 0, st>>>(topo->erow, g->col, x->m, x->n, x->y, hr, gb, ybr, L,
+                                       fc, grad_w);
       segmented<float>(x, g->row_ptr, topo->in, DotVal{grad_w, x->Pe}, WriteVec{T}, st);
       k_lin_edge_fin<<<gm, 256, 0, st>>>(topo->erow, x->m, T, x->Wa, grad_w);
     } else {
