@@ -31,6 +31,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "srk_internal.h"
 
@@ -56,6 +57,7 @@ struct Classes {
   int32_t *item_long = nullptr;   //   the node's index among the long lists
   int32_t *long_first = nullptr;  // first item and item count of each long list
   int32_t *long_count = nullptr;
+  int32_t *order = nullptr;       // the work units, heaviest first (see k_seg)
   int32_t n_small = 0, n_mid = 0, n_long = 0, n_items = 0;
 };
 
@@ -156,15 +158,17 @@ struct WriteVec {  // out[a] = sum
   __device__ __forceinline__ void operator()(int32_t a, float sum) const { out[a] = sum; }
 };
 
-// One segmented reduction over the work units, in this order: the chunks of
-// the lists longer than kMid (one warp each), the lists of kShort < len <=
-// kMid (one warp each), groups of 8 lists of kTiny < len <= kShort (two per
-// 8 lanes) and runs of 64 consecutive nodes, of which each lane reduces the
-// lists of two nodes that have at most kTiny entries (empty lists included).  Warp w
-// of the grid takes units w, w + W, w + 2W, ... (W warps), so every warp gets
-// a like mix of the classes.  A long list's chunk sums are added in chunk
-// order by the warp that finishes its last chunk, which then re-arms the
-// list's counter for the next launch.
+// One segmented reduction over the work units: the chunks of the lists
+// longer than kMid (one warp each), the lists of kShort < len <= kMid (one
+// warp each), groups of 8 lists of kTiny < len <= kShort (two per 8 lanes)
+// and runs of 64 consecutive nodes, of which each lane reduces the lists of
+// two nodes that have at most kTiny entries (empty lists included), numbered
+// in that order.  C.order lists them by rounds of loads, heaviest first, and
+// the W warps of the grid deal them out in snake order (warp w takes ranks
+// w, 2W - 1 - w, 2W + w, ...), so a warp with a heavy unit gets light ones
+// next.  A long list's chunk sums are added in chunk order by the warp that
+// finishes its last chunk, which then re-arms the list's counter for the
+// next launch.
 template <class T, class V, class W>
 __global__ void __launch_bounds__(kSegBlock)
 k_seg(const int32_t *__restrict__ ptr, int32_t n, Classes C, V val, W write,
@@ -173,7 +177,11 @@ k_seg(const int32_t *__restrict__ ptr, int32_t n, Classes C, V val, W write,
   const int64_t e1 = C.n_items, e2 = e1 + C.n_mid, e3 = e2 + ((int64_t)C.n_small + 7) / 8,
                 e4 = e3 + ((int64_t)n + 63) / 64;
   const int64_t W_all = ((int64_t)gridDim.x * blockDim.x) / 32;
-  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; u < e4; u += W_all) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  for (int64_t k = 0;; ++k) {
+    const int64_t r = k * W_all + ((k & 1) ? W_all - 1 - w : w);
+    if (r >= e4) break;  // every later rank is larger
+    const int64_t u = C.order[r];
     if (u < e1) {
       const T s = warp_sum(list_partial<T>(val, C.item_beg[u], C.item_end[u], lane, 32));
       if (lane == 0) {
@@ -537,6 +545,45 @@ static size_t class_layout(Classes *C, char *p, int32_t n, int64_t m) {
 static std::mutex topo_mu;
 
 // Builds g's linear topology on stream st and waits for it.
+// The static schedule of one direction's work units (k_seg): units sorted by
+// their rounds of 128 loads (4 per lane), ceil(len / 128) for chunks and mid
+// lists and 1 for the rest, descending; equal costs keep unit order.
+static cudaError_t build_order(Classes &C, int32_t n, cudaStream_t st) {
+  const int64_t e1 = C.n_items, e2 = e1 + C.n_mid, e3 = e2 + ((int64_t)C.n_small + 7) / 8,
+                e4 = e3 + ((int64_t)n + 63) / 64;
+  std::vector<int32_t> beg((size_t)C.n_items), end((size_t)C.n_items);
+  std::vector<int4> mid((size_t)C.n_mid);
+  cudaError_t e = cudaSuccess;
+  if (C.n_items > 0) {
+    e = cudaMemcpyAsync(beg.data(), C.item_beg, sizeof(int32_t) * beg.size(),
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(end.data(), C.item_end, sizeof(int32_t) * end.size(),
+                          cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess && C.n_mid > 0)
+    e = cudaMemcpyAsync(mid.data(), C.mid, sizeof(int4) * mid.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  constexpr int kRound = 128, kMaxCost = (kChunk > kMid ? kChunk : kMid) / kRound;
+  std::vector<uint8_t> cost((size_t)e4, 1);
+  for (int64_t u = 0; u < e2; ++u) {
+    const int64_t len = u < e1 ? (int64_t)end[(size_t)u] - beg[(size_t)u]
+                               : (int64_t)mid[(size_t)(u - e1)].z - mid[(size_t)(u - e1)].y;
+    const int64_t c = (len + kRound - 1) / kRound;
+    cost[(size_t)u] = (uint8_t)(c < 1 ? 1 : (c > kMaxCost ? kMaxCost : c));
+  }
+  std::vector<int32_t> order;
+  order.reserve((size_t)e4);
+  for (int c = kMaxCost; c >= 1; --c)
+    for (int64_t u = 0; u < e4; ++u)
+      if (cost[(size_t)u] == c) order.push_back((int32_t)u);
+  e = cudaMalloc(&C.order, sizeof(int32_t) * (size_t)(e4 > 0 ? e4 : 1));
+  if (e == cudaSuccess && e4 > 0)
+    e = cudaMemcpy(C.order, order.data(), sizeof(int32_t) * (size_t)e4, cudaMemcpyHostToDevice);
+  return e;
+}
+
 static int build_topo(const srk_graph *g, cudaStream_t st, srk_lin_topo **out) {
   const int dev = g->device;
   const int32_t n = g->n;
@@ -635,6 +682,14 @@ static int build_topo(const srk_graph *g, cudaStream_t st, srk_lin_topo **out) {
   T->out.n_long = hc[5];
   T->out.n_items = hc[6];
   T->out.n_small = hc[7];
+  if ((e = build_order(T->in, n, st)) != cudaSuccess ||
+      (e = build_order(T->out, n, st)) != cudaSuccess) {
+    if (T->in.order) cudaFree(T->in.order);
+    if (T->out.order) cudaFree(T->out.order);
+    cudaFree(T->block);
+    delete T;
+    return cuda_fail(e, "linear topology: unit order");
+  }
   *out = T;
   return SRK_OK;
 }
@@ -653,6 +708,8 @@ static int get_topo(const srk_graph *g, cudaStream_t st, const srk_lin_topo **ou
 
 void free_lin_topo(srk_graph *g) {
   if (!g || !g->lin) return;
+  if (g->lin->in.order) cudaFree(g->lin->in.order);
+  if (g->lin->out.order) cudaFree(g->lin->out.order);
   if (g->lin->block) cudaFree(g->lin->block);
   delete g->lin;
   g->lin = nullptr;
