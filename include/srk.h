@@ -226,7 +226,7 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
  * simplification: the paper's D is a correction matrix that is estimated.
  *   g      : the graph; its in-lists give the edges (edge e = entry e of col).
  *   edge_w : m positive finite FP32 weights aligned with col (device memory),
- *            or NULL for the weights given to srk_graph_load.
+ *            or NULL for the weights given to srk_graph_load (or when m = 0).
  *   s, c   : source (0 <= s < n) and decay (0 < c < 1).
  *   L      : last term, 0 <= L <= SRK_MAX_LEN.
  *   s_out  : n FP32 outputs (device memory).
@@ -250,7 +250,7 @@ int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s, double c,
  * of the forward recursions.
  *   ctx    : from srk_linear_fwd (not freed here; one backward at a time).
  *   grad_s : n FP32, dLoss/ds_out (device memory).
- *   grad_w : m FP32 outputs, dLoss/dw_e (device memory).  Because P is
+ *   grad_w : m FP32 outputs, dLoss/dw_e (device memory; may be NULL when m = 0).  Because P is
  *            invariant to scaling a node's in-weights, sum_{e in I(a)} w_e
  *            grad_w[e] = 0 for every node a (up to rounding).
  * Enqueues work on cuda_stream without synchronising.

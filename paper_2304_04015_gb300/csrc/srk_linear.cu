@@ -745,7 +745,8 @@ extern "C" int srk_linear_fwd(const srk_graph *g, const float *edge_w, int32_t s
   if (ctx_out) *ctx_out = nullptr;
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (!edge_w) edge_w = g->edge_w;
-  if (!edge_w) return fail(SRK_EINVAL, "no edge weights: pass edge_w or load the graph with them");
+  if (!edge_w && g->m > 0)
+    return fail(SRK_EINVAL, "no edge weights: pass edge_w or load the graph with them");
   if (s < 0 || s >= g->n) return fail(SRK_EINVAL, "source %d outside [0, %d)", s, g->n);
   if (!(c > 0.0 && c < 1.0)) return fail(SRK_EINVAL, "c = %g outside (0, 1)", c);
   if (L < 0 || L > SRK_MAX_LEN) return fail(SRK_EINVAL, "L = %d outside [0, %d]", L, SRK_MAX_LEN);
@@ -836,7 +837,7 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
                               void *cuda_stream) {
   clear_error();
   if (!x) return fail(SRK_EINVAL, "null context");
-  if (!grad_s || !grad_w) return fail(SRK_EINVAL, "null gradient pointer");
+  if (!grad_s || (!grad_w && x->m > 0)) return fail(SRK_EINVAL, "null gradient pointer");
   DeviceGuard guard(x->device);
   if (!is_device_ptr(grad_s) || (x->m > 0 && !is_device_ptr(grad_w)))
     return fail(SRK_EINVAL, "srk_linear_bwd takes device pointers");

@@ -124,6 +124,30 @@ def test_linear_invalid_weights_and_source(srk):
         graph.close()
 
 
+def test_linear_graph_without_edges(srk):
+    # P has no entries: s_vec = D e_s = (1 - c) e_s, and there is no weight
+    # to differentiate (the edge arrays are empty; no weights are needed)
+    import torch
+    dev = torch.device("cuda:0")
+    n = 70
+    rp = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    col = torch.zeros(0, dtype=torch.int32, device=dev)
+    graph = srk.srk_graph_load(rp, col)
+    try:
+        for s, L in ((5, 3), (69, 0)):
+            out = torch.full((n,), -1.0, dtype=torch.float32, device=dev)
+            ctx = srk.srk_linear_fwd(graph, None, s, C, L, out)
+            gw = torch.empty(0, dtype=torch.float32, device=dev)
+            srk.srk_linear_bwd(ctx, torch.ones(n, device=dev), gw)
+            torch.cuda.synchronize()
+            ref = np.zeros(n, dtype=np.float32)
+            ref[s] = np.float32(1.0 - C)
+            assert np.array_equal(out.cpu().numpy(), ref)
+            ctx.free()
+    finally:
+        graph.close()
+
+
 def hub_graph(n=12000, seed=5):
     """ER in-lists plus a node whose in-list holds every other node (a list of
     six 2048-entry chunks), a node with 300 in-neighbours (a warp-sized list)
