@@ -23,9 +23,9 @@
 // chunk order by the warp that finishes the list's last chunk, so no result
 // depends on timing.  The vectors are stored term-major, (L+1) x n: a gather
 // reads one contiguous term, whose most referenced entries (R-MAT's low ids)
-// share sectors and stay in L1.  The per-edge gradient pass reads node-major
-// copies of h and yb (one transpose each), so each source node's L values
-// come together.
+// share sectors and stay in L1.  The per-edge gradient pass reads, for each
+// source node, one node-major row of the pairs (h_{t+1}, yb_{t+1}) made by
+// one transpose, so each node's 2L values come together.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -414,39 +414,43 @@ __global__ void k_lin_scale(const float *__restrict__ in, float d, int32_t n,
     out[i] = d * in[i];
 }
 
-// Node-major copy of a term-major (S x n) matrix: block b moves nodes
-// [32 b, 32 b + 32) through shared memory (S x 33 floats), reading 32
-// consecutive nodes of a term and writing the 32 S consecutive outputs.
-__global__ void __launch_bounds__(256) k_lin_rows(const float *__restrict__ src, int32_t S,
-                                                  int32_t n, float *__restrict__ dst) {
-  extern __shared__ float tile[];
+// The node-major rows of the pairs (h_{t+1}[u], yb_{t+1}[u]), t < L, from the
+// term-major h and yb: hy[u][t] = {h[(t+1) n + u], yb[(t+1) n + u]}.  Block b
+// moves nodes [32 b, 32 b + 32) through shared memory (2 L x 33 floats),
+// reading 32 consecutive nodes of a term and writing the 32 L consecutive
+// pairs.
+__global__ void __launch_bounds__(256) k_lin_pairs(const float *__restrict__ h,
+                                                   const float *__restrict__ yb, int32_t L,
+                                                   int32_t n, float2 *__restrict__ hy) {
+  extern __shared__ float tile[];  // [0, 33 L): h terms 1..L; [33 L, 66 L): yb terms
   const int64_t a0 = (int64_t)blockIdx.x * 32;
   const int na = (int)((int64_t)n - a0 < 32 ? (int64_t)n - a0 : 32);
-  for (int q = threadIdx.x; q < S * 32; q += blockDim.x) {
+  for (int q = threadIdx.x; q < L * 32; q += blockDim.x) {
     const int t = q >> 5, j = q & 31;
-    if (j < na) tile[t * 33 + j] = src[(int64_t)t * n + a0 + j];
+    if (j < na) {
+      tile[t * 33 + j] = h[(int64_t)(t + 1) * n + a0 + j];
+      tile[(L + t) * 33 + j] = yb[(int64_t)(t + 1) * n + a0 + j];
+    }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < na * S; q += blockDim.x) {
-    const int j = q / S, t = q - j * S;
-    dst[(a0 + j) * S + t] = tile[t * 33 + j];
+  for (int q = threadIdx.x; q < na * L; q += blockDim.x) {
+    const int j = q / L, t = q - j * L;
+    hy[(a0 + j) * L + t] = make_float2(tile[t * 33 + j], tile[(L + t) * 33 + j]);
   }
 }
 
 // G_e for every edge e = (u -> a), edge-parallel.  gb and y are term-major
 // (consecutive edges mostly share a, so a warp reads one word per term); h
-// and yb come as node-major rows hr, ybr (u is scattered, so a thread reads
-// u's L values from one row).
+// and yb come as u's row of pairs in hy (u is scattered, so a thread reads
+// its 2 L values from one row).
 __global__ void k_lin_edge_G(const int32_t *__restrict__ erow, const int32_t *__restrict__ col,
                              int64_t m, int32_t n, const float *__restrict__ y,
-                             const float *__restrict__ hr, const float *__restrict__ gb,
-                             const float *__restrict__ ybr, int32_t L, float c,
-                             float *__restrict__ G) {
-  const int32_t S = L + 1;
+                             const float2 *__restrict__ hy, const float *__restrict__ gb,
+                             int32_t L, float c, float *__restrict__ G) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = erow[k], u = col[k];
-    const float *hu = hr + u * S, *ybu = ybr + u * S;
+    const float2 *hyu = hy + u * L;
     float g = 0.0f;
     for (int t0 = 0; t0 < L; t0 += 4) {  // four terms' loads in flight
       float gv[4], yv[4], hv[4], bv[4];
@@ -454,10 +458,11 @@ __global__ void k_lin_edge_G(const int32_t *__restrict__ erow, const int32_t *__
       for (int j = 0; j < 4; ++j) {
         const int t = t0 + j;
         const bool ok = t < L;
+        const float2 p = ok ? hyu[t] : make_float2(0.0f, 0.0f);
         gv[j] = ok ? gb[(int64_t)t * n + a] : 0.0f;
         yv[j] = ok ? y[(int64_t)t * n + a] : 0.0f;
-        hv[j] = ok ? hu[t + 1] : 0.0f;
-        bv[j] = ok ? ybu[t + 1] : 0.0f;
+        hv[j] = p.x;
+        bv[j] = p.y;
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {  // t ascending; the padding terms add exact zeros
@@ -852,9 +857,11 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
   cudaMemPool_t mp = pool(dev);
   if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
   float *gb = nullptr;
+  // gb, yb (term-major), the rows of pairs (2 L n floats) and T_a
   cudaError_t e = cudaMallocFromPoolAsync((void **)&gb, sizeof(float) * (4 * vec + n), mp, st);
   if (e != cudaSuccess) return cuda_fail(e, "srk_linear_bwd: allocation");
-  float *yb = gb + vec, *hr = gb + 2 * vec, *ybr = gb + 3 * vec, *T = gb + 4 * vec;
+  float *yb = gb + vec, *T = gb + 2 * vec;
+  float2 *hy = reinterpret_cast<float2 *>(gb + 2 * vec + n + (n & 1));
   const int gn = grid_of((int64_t)n, 256, dev), gm = grid_of(x->m, 256, dev);
   const float fc = (float)x->c, d = (float)(1.0 - x->c);
   // gb_0 = g
@@ -869,14 +876,15 @@ extern "C" int srk_linear_bwd(srk_linear_ctx *x, const float *grad_s, float *gra
   }
   if (x->m > 0) {
     if (L >= 1) {
-      // node-major rows of h and yb, G_e into grad_w, T_a = sum G_e P_e per
-      // in-list, then the normalisation
-      const int gr = (int)((n + 31) / 32);
-      const size_t tile = sizeof(float) * 33 * (size_t)S;
-      k_lin_rows<<<gr, 256, tile, st>>>(x->h, S, x->n, hr);
-      k_lin_rows<<<gr, 256, tile, st>>>(yb, S, x->n, ybr);
-      k_lin_edge_G<<<gm, 256, 0, st>>>(topo->erow, g->col, x->m, x->n, x->y, hr, gb, ybr, L,
-                                       fc, grad_w);
+      // the rows of pairs (h_{t+1}, yb_{t+1}), G_e into grad_w, T_a = sum
+      // G_e P_e per in-list, then the normalisation
+      const size_t tile = sizeof(float) * 66 * (size_t)L;
+      if (tile > 48 * 1024)
+        cudaFuncSetAttribute(k_lin_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile);
+      k_lin_pairs<<<(int)((n + 31) / 32), 256, tile, st>>>(x->h, yb, L, x->n, hy);
+      k_lin_edge_G<<<gm, 256, 0, st>>>(topo->erow, g->col, x->m, x->n, x->y, hy, gb, L, fc,
+                                       grad_w);
       segmented<float>(x, g->row_ptr, topo->in, DotVal{grad_w, x->Pe}, WriteVec{T}, st);
       k_lin_edge_fin<<<gm, 256, 0, st>>>(topo->erow, x->m, T, x->Wa, grad_w);
     } else {
