@@ -163,12 +163,12 @@ struct WriteVec {  // out[a] = sum
 // warp each), groups of 8 lists of kTiny < len <= kShort (two per 8 lanes)
 // and runs of 64 consecutive nodes, of which each lane reduces the lists of
 // two nodes that have at most kTiny entries (empty lists included), numbered
-// in that order.  C.order lists them by rounds of loads, heaviest first, and
-// the W warps of the grid deal them out in snake order (warp w takes ranks
-// w, 2W - 1 - w, 2W + w, ...), so a warp with a heavy unit gets light ones
-// next.  A long list's chunk sums are added in chunk order by the warp that
-// finishes its last chunk, which then re-arms the list's counter for the
-// next launch.
+// in that order.  C.order lists them by rounds of loads, heaviest first.  With
+// a warp per unit (the launch in segmented()) warp w takes rank w; a smaller
+// grid of W warps deals the ranks out in snake order (warp w takes w,
+// 2W - 1 - w, 2W + w, ...).  A long list's chunk sums are added in chunk
+// order by the warp that finishes its last chunk, which then re-arms the
+// list's counter for the next launch.
 template <class T, class V, class W>
 __global__ void __launch_bounds__(kSegBlock)
 k_seg(const int32_t *__restrict__ ptr, int32_t n, Classes C, V val, W write,
@@ -493,8 +493,11 @@ static int grid_of(int64_t work, int per_block, int dev, int per_sm = 8) {
   return (int)(want < 1 ? 1 : (want > cap ? cap : want));
 }
 
-// Segmented reduction over the lists of ptr (size classes C): one launch of
-// at most 8 blocks of 8 warps per SM (all resident).
+// Segmented reduction over the lists of ptr (size classes C): one launch
+// with a warp per work unit.  Blocks take the units heaviest first (C.order)
+// and the block scheduler starts each next block on the first SM with room,
+// which makes a greedy longest-first schedule (measured faster than a grid of
+// resident blocks dealing the units among themselves).
 template <class T, class V, class W>
 static void segmented(srk_linear_ctx *x, const int32_t *ptr, const Classes &C, V val, W write,
                       cudaStream_t st) {
@@ -502,8 +505,6 @@ static void segmented(srk_linear_ctx *x, const int32_t *ptr, const Classes &C, V
                         ((int64_t)x->n + 63) / 64;
   const int warps = kSegBlock / 32;
   int64_t blocks = (units + warps - 1) / warps;
-  const int64_t cap = (int64_t)sm_count(x->device) * 8;
-  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k_seg<T><<<(int)blocks, kSegBlock, 0, st>>>(ptr, x->n, C, val, write,
                                               reinterpret_cast<T *>(x->part), x->done);
