@@ -467,8 +467,8 @@ def run_linear(args, rank, world):
     achieved = (fwd_bytes + bwd_bytes) * args.steps / t / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "forward+backward (all kernels; the k_seg gathers are ~75 % of "
-                          "device time in the launch list)",
+                "kernel": "forward+backward (all kernels; the k_seg gathers are about two "
+                          "thirds of device time in the launch list)",
                 "peak_kind": peak_kind + " (HBM copy)",
                 "bytes_per_unit": fwd_bytes + bwd_bytes, "unit_name": "forward+backward"}
     base = None
