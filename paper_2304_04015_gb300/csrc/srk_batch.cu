@@ -338,6 +338,39 @@ static void launch_targets_t(int shape, int grid, int block, size_t smem, cudaSt
 #undef SRK_KB_LAUNCH
 }
 
+// Shared memory of the target kernel in launch shape `shape`: two rows of
+// Lmax + 3 words per warp.
+static size_t target_smem(int shape, int Lmax) {
+  return sizeof(int32_t) * 2 * (size_t)(Lmax + 3) * (size_t)(kShapes[shape].block / 32);
+}
+
+// Lets every launch shape of layout kLayout take `bytes` of dynamic shared
+// memory (above the default 48 KB a kernel must opt in).  Not a stream
+// operation, so it runs before any capture.
+template <int kLayout>
+static cudaError_t allow_smem_t(size_t bytes) {
+  const int b = (int)bytes;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void *f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  };
+  set((const void *)kb_target_walks<256, 8, kLayout>);
+  set((const void *)kb_target_walks<512, 4, kLayout>);
+  set((const void *)kb_target_walks<128, 16, kLayout>);
+  set((const void *)kb_target_walks<1024, 2, kLayout>);
+  set((const void *)kb_target_walks<256, 6, kLayout>);
+  return e;
+}
+
+static cudaError_t allow_smem(int layout, int Lmax) {
+  size_t most = 0;
+  for (int sh = 0; sh < kNumShapes; ++sh) most = std::max(most, target_smem(sh, Lmax));
+  if (most <= 48 * 1024) return cudaSuccess;
+  return layout == kWide ? allow_smem_t<kWide>(most)
+         : layout == kCsr ? allow_smem_t<kCsr>(most)
+                          : allow_smem_t<kNarrow>(most);
+}
+
 static void launch_targets(int layout, int shape, int sms, cudaStream_t st, const BatchArgs &A,
                            const int32_t *act, int32_t n_act, const int32_t *act_src,
                            const int32_t *n_act_src, unsigned long long *ctr,
@@ -345,7 +378,7 @@ static void launch_targets(int layout, int shape, int sms, cudaStream_t st, cons
   const Shape sh = kShapes[shape];
   const int grid = sms * sh.per_sm;
   const int32_t rw = Lmax + 3;
-  const size_t smem = sizeof(int32_t) * 2 * (size_t)rw * (size_t)(sh.block / 32);
+  const size_t smem = target_smem(shape, Lmax);
   if (layout == kWide)
     launch_targets_t<kWide>(shape, grid, sh.block, smem, st, A, act, n_act, act_src,
                             n_act_src, ctr, limit, rw);
@@ -533,6 +566,11 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
                                             (int64_t)sms * 16);
       kb_prefill<<<gp, 256, 0, s2>>>(d_src, kb, (int32_t)n);
     };
+    if ((e = allow_smem(g->layout, Lmax)) != cudaSuccess) {
+      rc = cuda_fail(e, "batched query: shared memory of the target kernel");
+      cudaFreeAsync(base, st);
+      break;
+    }
     // autotune the persistent kernel's launch shape on the first batch
     int shape = g->batch_cfg;
     if (shape < 0 || shape >= kNumShapes) {
@@ -548,9 +586,10 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
         cudaEventRecord(t0, st);
         launch_targets(g->layout, sh, sms, st, A, g->act, g->n_act, d_act_src, d_act_src + kb,
                        d_ctr, trial, Lmax);
+        const bool launched = cudaGetLastError() == cudaSuccess;  // a shape that cannot run
         cudaEventRecord(t1, st);
         float ms = 0.f;
-        if (cudaEventSynchronize(t1) == cudaSuccess &&
+        if (cudaEventSynchronize(t1) == cudaSuccess && launched &&
             cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms < best) {
           best = ms;
           shape = sh;

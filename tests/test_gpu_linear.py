@@ -65,7 +65,9 @@ def test_small_graph_against_reverse_mode_oracle(srk):
     from oracle import linear
     rp, col, w = weighted("er", 500, 3)
     g = np.random.default_rng(4).normal(size=500)
-    for s, L in ((0, 10), (17, 3), (5, 1)):
+    # L = 200: the gradient's transpose tile (66 L floats) needs more than
+    # 48 KB of shared memory
+    for s, L in ((0, 10), (17, 3), (5, 1), (3, 200)):
         out, gr = run_gpu(srk, rp, col, w, s, L, g)
         ref_g, ref_s = linear.grad(rp, col, w.astype(np.float64), 500, s, C, L, g)
         check_forward(out, ref_s)

@@ -556,6 +556,33 @@ def test_hub_headers_bit_exact(srk):
         assert np.array_equal(rows[layout][1], rows["narrow"][1])
 
 
+def test_multi_source_long_walks_shared_memory(srk):
+    # L = 250: in its 1024-thread launch shape the batched kernel's per-warp
+    # rows take ~65 KB of shared memory, above the 48 KB a kernel gets without
+    # opting in; the autotuner (first call on a fresh handle) tries every shape
+    import torch
+    rp, col = er_graph(1000, 5.0, 1)
+    n = rp.size - 1
+    dev = torch.device("cuda:0")
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        kw = dict(z_override=500.0, L_override=250)
+        src = [0, 17, 423]
+        multi = torch.empty((3, n), dtype=torch.float64, device=dev)
+        st = srk.SrkStats()
+        srk.srk_multi_source(g, src, C, [0.1] * 3, 9, multi, stats=st, **kw)
+        torch.cuda.synchronize()
+        assert st.L == 250 and 0 <= st.batch_shape < 5
+        for i, s in enumerate(src):
+            one = torch.empty(n, dtype=torch.float64, device=dev)
+            srk.srk_single_source(g, s, C, 0.1, 9, one, **kw)
+            torch.cuda.synchronize()
+            assert torch.equal(one, multi[i])
+        assert float(multi.sum()) > 3.0  # some targets besides the sources score
+    finally:
+        g.close()
+
+
 def test_degenerate_graphs_and_calls(srk):
     import torch
     dev = torch.device("cuda:0")
