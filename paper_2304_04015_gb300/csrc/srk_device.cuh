@@ -165,7 +165,7 @@ __device__ __forceinline__ int32_t node_start(const Adj &G, const int32_t *, int
   return deg < G.dmax ? x + 1 : (int32_t)G.adj[x + 1];
 }
 
-// The wide packed adjacency, for graphs whose positions need more than 27
+// The wide packed adjacency, for graphs whose positions need more than 28
 // bits (the degree code of a 32-bit entry would then be too small to spare
 // most steps a second random read): 8-byte words at positions
 // pos(v) = v + row_ptr[v], adj[pos(v)] = {0, |I(v)|}; entry k of v's list,

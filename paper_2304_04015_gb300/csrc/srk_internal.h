@@ -22,12 +22,12 @@ struct srk_graph {
   // the k-th in-neighbour y as (min(|I(y)|, deg_max) << pos_bits) | npos[y],
   // so a walk step learns the next node's degree from the entry it reads and
   // reads a header only at a hub.
-  // Wide layout (layout = 1, chosen when positions need more than 27 bits
-  // or forced by SRK_ADJ_WIDE): 2 (n + m) words forming 8-byte entries at
+  // Wide layout (layout = 1, chosen when n + m needs more than 28 bits or
+  // forced by SRK_ADJ_WIDE): 2 (n + m) words forming 8-byte entries at
   // positions v + row_ptr[v], adj[pos(v)] = {0, |I(v)|} and entries
   // {pos(y), |I(y)|}, so a step never reads a header.  CSR layout (layout =
-  // 2, at 27 bits or forced by SRK_ADJ_CSR): no packed copy; nodes are their
-  // ids and a step reads row_ptr and col.
+  // 2, only when forced by SRK_ADJ_CSR): no packed copy; nodes are their ids
+  // and a step reads row_ptr and col.
   uint32_t *adj = nullptr;
   int32_t *npos = nullptr;  // narrow layout: positions, n (owned)
   int32_t n_hubs = 0;       // narrow layout: H
