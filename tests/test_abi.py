@@ -73,6 +73,39 @@ def test_graph_load_rejects_bad_arguments_without_touching_the_device(lib):
                                  ctypes.c_uint64(1), None, None, None, None, None) == srk.SRK_EINVAL
 
 
+def test_null_handles_are_refused_on_the_host(lib):
+    # every entry point checks its handle or output pointer before any CUDA
+    # call; releasing NULL is allowed
+    import paper_2304_04015_gb300 as srk
+    L = srk._lib
+    n, m, lay, adm = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    src = (ctypes.c_int32 * 1)(0)
+    eps = (ctypes.c_double * 1)(0.1)
+    report = srk.SrkServerReport()
+    assert L.srk_graph_free(None) == srk.SRK_OK
+    assert L.srk_linear_ctx_free(None) == srk.SRK_OK
+    assert L.srk_server_destroy(None) == srk.SRK_OK
+
+    def refused(rc, msg):
+        assert rc == srk.SRK_EINVAL and msg in L.srk_last_error()
+
+    refused(L.srk_graph_info(None, ctypes.byref(n), ctypes.byref(m)), b"null graph")
+    refused(L.srk_graph_layout(None, ctypes.byref(lay)), b"null argument")
+    refused(L.srk_single_source_noalloc(None, 0, 0.6, 0.1, 1, None, None, None, None, None),
+            b"null graph")
+    refused(L.srk_multi_source(None, ctypes.cast(src, ctypes.c_void_p), 1, 0.6,
+                               ctypes.cast(eps, ctypes.c_void_p), 1, None, None, None, None),
+            b"null graph")
+    refused(L.srk_linear_fwd(None, None, 0, 0.6, 3, None, None, None), b"null graph")
+    refused(L.srk_linear_bwd(None, None, None, None), b"null context")
+    refused(L.srk_server_create(None, 0, 0, 1, 0.0, None), b"out is null")
+    refused(L.srk_server_submit(None, 0, 0, 0.6, 0.1, 1, None, 0, ctypes.byref(adm)),
+            b"null server")
+    refused(L.srk_server_drain(None), b"null server")
+    refused(L.srk_server_stats(None, ctypes.byref(report)), b"null argument")
+    refused(L.srk_probe_gather(None, 0, 1, 1, None, None, None), b"bad arguments")
+
+
 def test_build_entry_point():
     import __graft_entry__ as g
     g.build()
