@@ -7,19 +7,26 @@ self-loops, int32 in-neighbour CSR; c = 0.6, eps = 0.02 (z = ln(2n) /
 (2 (eps - 3/n)^2)), 64 uniformly drawn sources, one query per launch.  A step
 is one full query (steps a1-a5) for the next source of the list.
 
-Timing: W untimed warm-up queries, then K timed ones.  Every query is timed
-with CUDA events on its stream; the 256 MB L2 flush written between queries
-lies outside those intervals.  The dominant kernel (target walks, step a4) is
-timed with events the library records around its launch.  ``e2e`` repeats the
-K queries through the same C-ABI call with host output buffers, so the timed
-region includes the device-to-host copy of every score vector.
+A step is one pass over all 64 sources (64 queries), so the timed set does
+not depend on the step count.  Timing: W untimed warm-up passes, then K timed
+ones.  Every query is timed with CUDA events on its stream; the 256 MB L2
+flush written between queries lies outside those intervals.  The dominant
+kernel (target walks, step a4) is timed with events the library records
+around its launch.  ``e2e`` repeats the K passes through the same C-ABI call
+with host output buffers, so the timed region includes the device-to-host
+copy of every score vector.  The roofline block names the bound that binds:
+with the adjacency inside the L2 it is the random-gather rate measured live
+by the probe on an array of the adjacency's size (the HBM-copy fraction is
+kept beside it, labelled).
 
 ``--impl reference`` times the CPU oracle (the plain C restatement of the
 method, OpenMP over targets on the host cores) on a bounded sample of the same
 workload and prints the same JSON line with ``"impl": "reference"``.
 
-Multi-GPU (torchrun): sources are sharded across ranks with no data-path
-collective (weak scaling); rank 0 prints the aggregate.
+Multi-GPU (torchrun): every rank runs its own 64-source list with no
+data-path collective (weak scaling); rank 0 prints the aggregate.
+``--workload split`` instead splits every query over the ranks by target
+range (the owner rule of Section 5.5) and all-gathers the score slices.
 """
 from __future__ import annotations
 
@@ -52,7 +59,8 @@ WORKLOAD = "rmat20_ef16_eps0.02_64src_one_query_per_launch"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=3,
+                    help="timed steps; a step is one pass over the 64 sources")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -61,7 +69,7 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-probe", action="store_true")
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "batch", "linear", "serve", "probe"],
+                    choices=["plain", "batch", "linear", "serve", "probe", "split"],
                     help="plain: the R-MAT 20 one-query-per-launch workload; batch: "
                          "batched multi-source on R-MAT --batch-scale vs the plain path")
     ap.add_argument("--batch-scale", type=int, default=24)
@@ -87,12 +95,6 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
-
-
-def shard_sources(sources, rank: int, world: int):
-    """Sources of this rank: queries are independent, so ranks take disjoint
-    strided slices and exchange nothing but timings (weak scaling)."""
-    return sources[rank::world] if world > 1 else sources
 
 
 def max_over_ranks(value: float, pg, device) -> float:
@@ -597,39 +599,115 @@ def run_serve(args, rank, world):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores, on the same workload: a step is one pass
+    over the 64 sources, each query on a uniform sample of targets with its
+    time scaled by n / targets (the whole run stays within a few minutes)."""
     if rank != 0:
         return 0
     rp, col, sources = make_workload()
-    budget = max(2.0, min(20.0, 60.0 / max(args.steps + args.warmup, 1)))
     from oracle import sampler
     n = rp.size - 1
     rng = np.random.default_rng(11)
-    k = max(256, int(n * 0.002))
-    times = []
+    k = max(64, int(n * 0.0003))
+    threads = os.cpu_count() or 1
+    pass_s = []
     for i in range(args.warmup + args.steps):
-        s = int(sources[i % len(sources)])
-        targets = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int32)
-        t0 = time.perf_counter()
-        sampler.run(rp, col, n, s, C, EPS, QUERY_SEED, targets=targets,
-                    threads=os.cpu_count() or 1)
-        dt = time.perf_counter() - t0
+        t_pass = 0.0
+        for s in sources:
+            targets = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int32)
+            t0 = time.perf_counter()
+            sampler.run(rp, col, n, int(s), C, EPS, QUERY_SEED, targets=targets,
+                        threads=threads)
+            t_pass += (time.perf_counter() - t0) * n / k
         if i >= args.warmup:
-            times.append(dt * n / k)
-    per_query = float(np.mean(times))
-    value = 1.0 / per_query
+            pass_s.append(t_pass)
+    per_step = float(np.mean(pass_s))
+    value = len(sources) / per_step
+    sample = ("%d of %d uniform targets per query, every source of the 64-source list per "
+              "step, times scaled by n/targets" % (k, n))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_query * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "%d uniform targets per query, time scaled by n/targets" % k},
-            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": os.cpu_count(),
-                             "kind": "oracle",
-                             "sample": "%d of %d targets per query, %d queries" % (k, n, args.steps)},
+            "config": {"workload": WORKLOAD, "sources_per_step": len(sources),
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0},
-            "budget_s": budget}
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_split(args, rank, world):
+    """One query split across ranks by target range (the owner rule of
+    Section 5.5, paper_2304_04015_gb300.split): every rank loads the whole
+    graph, walks the targets it owns and the score slices are all-gathered
+    (NCCL); a step is one pass over the 64 sources, each query split over
+    all ranks (strong scaling: the work per step is fixed)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    else:
+        pg = None
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_04015_gb300 as srk
+    from paper_2304_04015_gb300.split import owner_range, split_query
+    rp, col, sources = make_workload()
+    n = rp.size - 1
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                           layout=args.layout)
+    for _ in range(args.warmup):
+        for s in sources:
+            split_query(g, int(s), C, EPS, QUERY_SEED, rank, world)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.steps):
+        for s in sources:
+            full = split_query(g, int(s), C, EPS, QUERY_SEED, rank, world)
+    ev[1].record()
+    ev[1].synchronize()
+    t = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, pg, dev)
+    b, e = owner_range(n, rank, world)
+    line = {"metric": "single-source SimRank queries/s at eps=0.02, one query split over "
+                      "ranks by target range", "value": args.steps * len(sources) / t,
+            "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + "_target_split",
+                       "targets_of_rank0": [b, e], "gather": "one all_gather of FP64 slices",
+                       "l2": "not flushed between queries"},
+            "last_score_sum": float(full.sum())}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def adjacency_bytes(layout: str, n: int, m: int) -> int:
+    """Bytes of the adjacency the walk steps read, by layout: 4-byte entries
+    (plus the hub table, a few KB to MB), 8-byte entries at n + m positions,
+    or the CSR itself."""
+    return {"narrow": 4 * m, "wide": 8 * (n + m), "csr": 4 * (n + 1) + 4 * m}[layout]
+
+
+def source_list(n: int, rank: int):
+    """The 64 sources of one rank: rank 0 takes the workload's list (seed 2);
+    rank r > 0 draws its own 64 from seed 2 + 1000 r, so every rank runs a
+    full list per step (weak scaling)."""
+    from srk_inputs import uniform_sources
+    return uniform_sources(n, N_SOURCES, seed=SOURCE_SEED + 1000 * rank)
 
 
 def main():
@@ -645,6 +723,8 @@ def main():
         return run_serve(args, rank, world) if rank == 0 else 0
     if args.workload == "probe":
         return run_probe(args, rank, world) if rank == 0 else 0
+    if args.workload == "split":
+        return run_split(args, rank, world)
 
     import torch
     if not torch.cuda.is_available():
@@ -663,14 +743,17 @@ def main():
     import paper_2304_04015_gb300 as srk
 
     t_gen = time.perf_counter()
-    rp, col, sources = make_workload()
+    rp, col, _ = make_workload()
     t_gen = time.perf_counter() - t_gen
     n, m = rp.size - 1, col.size
-    my_sources = shard_sources(sources, rank, world)
+    my_sources = [int(x) for x in source_list(n, rank)]
+    deg = np.diff(rp)
+    n_src = len(my_sources)
 
     rp_d = torch.from_numpy(rp).to(dev)
     col_d = torch.from_numpy(col).to(dev)
     g = srk.srk_graph_load(rp_d, col_d, layout=args.layout)
+    layout = srk.srk_graph_layout(g)
     stream = torch.cuda.current_stream(dev)
     scores = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -680,27 +763,30 @@ def main():
         e.record(stream)   # creates the CUDA events
     torch.cuda.synchronize()
 
-    def query(i, out, timing=None, stats=None):
-        s = int(my_sources[i % len(my_sources)])
+    def query(s, out, timing=None, stats=None):
         srk.srk_single_source(g, s, C, EPS, QUERY_SEED, out, stats=stats,
                               timing_events=timing, stream=stream,
                               literal_shuffle=args.literal_shuffle,
                               warmup_rule=args.warmup_rule)
 
-    # warm-up
-    for i in range(args.warmup):
-        query(i, scores)
+    # warm-up: W passes over the source list
+    for _ in range(args.warmup):
+        for s in my_sources:
+            query(s, scores)
     torch.cuda.synchronize()
 
-    # per-query step counts (one untimed pass: the counters need a sync)
+    # per-source step counts (one untimed pass; the counters need a sync;
+    # every pass repeats the same queries, so the counts are per pass)
     stats_steps = []
-    for i in range(args.steps):
+    for s in my_sources:
         st = srk.SrkStats()
-        query(i, scores, stats=st)
+        query(s, scores, stats=st)
         stats_steps.append((st.target_steps, st.source_steps, st.n_walks, st.n_active_pairs,
                             st.z, st.L))
     torch.cuda.synchronize()
 
+    # timed: K passes; each query bracketed by events on its stream, the L2
+    # flush between queries outside the intervals
     clocks = ClockSampler(local)
     if pg:
         pg.barrier()
@@ -708,14 +794,15 @@ def main():
     clocks.start()
     q_ms, k_ms = [], []
     t_wall = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)          # evict the graph from L2 between queries
-        ev_q[0].record(stream)
-        query(i, scores, timing=ev_k)
-        ev_q[1].record(stream)
-        ev_q[1].synchronize()
-        q_ms.append(ev_q[0].elapsed_time(ev_q[1]))
-        k_ms.append(ev_k[0].elapsed_time(ev_k[1]))
+    for step in range(args.steps):
+        for i, s in enumerate(my_sources):
+            flush.fill_((step * n_src + i) & 0xFF)   # evict the graph from L2 between queries
+            ev_q[0].record(stream)
+            query(s, scores, timing=ev_k)
+            ev_q[1].record(stream)
+            ev_q[1].synchronize()
+            q_ms.append(ev_q[0].elapsed_time(ev_q[1]))
+            k_ms.append(ev_k[0].elapsed_time(ev_k[1]))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     if pg:
@@ -723,51 +810,51 @@ def main():
     clk = clocks.stop()
 
     total_ms = max_over_ranks(float(np.sum(q_ms)), pg, dev)
-    queries = args.steps * world
+    queries = args.steps * n_src * world
     value = queries / (total_ms / 1e3)
-    tgt_steps = sum(x[0] for x in stats_steps)
-    src_steps = sum(x[1] for x in stats_steps)
+    tgt_steps = args.steps * sum(x[0] for x in stats_steps)
+    src_steps = args.steps * sum(x[1] for x in stats_steps)
     steps_per_s = (tgt_steps + src_steps) * world / (total_ms / 1e3)
 
-    # e2e: the same queries through the C ABI with host output buffers
+    # e2e: the same K passes through the C ABI with host output buffers
     e2e = None
     if not args.skip_e2e:
         host_scores = torch.empty(n, dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
         e2e_s = 0.0
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            query(i, host_scores.numpy())     # D2H copy + sync inside the call
-            e2e_s += time.perf_counter() - t0
+        for step in range(args.steps):
+            for i, s in enumerate(my_sources):
+                flush.fill_((step * n_src + i) & 0xFF)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                query(s, host_scores.numpy())     # D2H copy + sync inside the call
+                e2e_s += time.perf_counter() - t0
         e2e_s = max_over_ranks(e2e_s, pg, dev)
         e2e = {"value": queries / e2e_s, "unit": "queries/s",
-               "h2d_bytes_per_step": 3108,
-               "d2h_bytes_per_step": 8 * n,
+               "h2d_bytes_per_step": 3108 * n_src,
+               "d2h_bytes_per_step": 8 * n * n_src,
                "note": "graph resident (loaded once); per query the host passes "
                        "(s, c, eps, seed) and the 3108-byte sample-count table as "
-                       "kernel arguments and reads back n FP64 scores"}
+                       "kernel arguments and reads back n FP64 scores; a step is "
+                       "%d queries" % n_src}
 
-    peak, peak_kind = load_peaks()
+    peak_hbm, peak_kind = load_peaks()
     kern_s = float(np.sum(k_ms)) / 1e3
     target_steps_per_s = tgt_steps / kern_s
-    achieved = tgt_steps * BYTES_PER_STEP / kern_s / 1e9
+    hbm_achieved = tgt_steps * BYTES_PER_STEP / kern_s / 1e9
     per_step = recorded_traffic()
-    traffic = per_step * tgt_steps / args.steps if per_step is not None else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_target_walks", "peak_kind": peak_kind + " (HBM copy)",
-                "bytes_per_unit": BYTES_PER_STEP, "unit_name": "target-walk step",
-                "kernel_ms_per_launch": float(np.mean(k_ms)),
-                "kernel_share_of_query": float(np.sum(k_ms) / np.sum(q_ms))}
+    launches = args.steps * n_src
+    traffic = per_step * tgt_steps / launches if per_step is not None else None
+    adj_b = adjacency_bytes(layout, n, m)
+    l2_b = torch.cuda.get_device_properties(dev).L2_cache_size
     gather = None
+    l2_rate = None
     if not args.skip_probe:
         ops = (srk.SRK_PROBE_DEFAULT, srk.SRK_PROBE_CG, srk.SRK_PROBE_NC, srk.SRK_PROBE_CA)
-        by_op = gather_probe(srk, torch, dev, n + m, ops)       # graph-sized array
+        by_op = gather_probe(srk, torch, dev, adj_b // 4, ops)     # graph-sized array
         l2_rate = by_op[0]
-        hbm_rate = gather_probe(srk, torch, dev, 1 << 30)[0]    # 4 GB array
-        l1_rate = gather_probe(srk, torch, dev, 1 << 12)[0]     # 16 KB array (L1 hits)
+        hbm_rate = gather_probe(srk, torch, dev, 1 << 30)[0]       # 4 GB array
+        l1_rate = gather_probe(srk, torch, dev, 1 << 12)[0]        # 16 KB array (L1 hits)
         gather = {"probe_gathers_per_s_graph_sized": l2_rate,
                   "probe_gathers_per_s_4GB": hbm_rate,
                   "probe_gathers_per_s_16KB": l1_rate,
@@ -776,13 +863,40 @@ def main():
                   "kernel_steps_per_s": target_steps_per_s,
                   "frac_of_graph_sized_probe": target_steps_per_s / l2_rate,
                   "note": "one scattered 4-byte adjacency read per target-walk step; "
-                          "probe = srk_probe_gather, independent random loads at full occupancy"}
+                          "probe = srk_probe_gather, independent random loads at full "
+                          "occupancy on an array the size of the adjacency"}
+    fits_l2 = adj_b <= l2_b
+    hbm_frac = hbm_achieved / peak_hbm
+    common = {"kernel": "k_target_walks", "traffic": traffic,
+              "traffic_unit": "DRAM bytes per launch (ncu, recorded for these kernel sources)",
+              "kernel_ms_per_launch": float(np.mean(k_ms)),
+              "kernel_share_of_query": float(np.sum(k_ms) / np.sum(q_ms)),
+              "adjacency_bytes": adj_b, "l2_bytes": l2_b,
+              "hbm_copy": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s",
+                           "frac": hbm_frac, "peak_kind": peak_kind + " (HBM copy)",
+                           "bytes_per_unit": BYTES_PER_STEP,
+                           "unit_name": "target-walk step (row_ptr pair + one entry)"}}
+    if l2_rate is not None:
+        roofline = {"bound": "l2_gather" if fits_l2 else "hbm_gather",
+                    "achieved": target_steps_per_s / 1e9, "peak": l2_rate / 1e9,
+                    "unit": "Gloads/s", "frac": target_steps_per_s / l2_rate,
+                    "peak_kind": "measured live: random 4-byte gather probe on an array the "
+                                 "size of the adjacency (%d MB)" % (adj_b >> 20),
+                    "unit_name": "target-walk step (one dependent scattered adjacency load)",
+                    **common}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": peak_hbm,
+                    "unit": "GB/s", "frac": hbm_frac,
+                    "peak_kind": peak_kind + " (HBM copy)",
+                    "bytes_per_unit": BYTES_PER_STEP, "unit_name": "target-walk step",
+                    **common}
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(rp, col, sources, args.cpu_seconds,
+        base = cpu_baseline(rp, col, my_sources, args.cpu_seconds,
                             literal_shuffle=args.literal_shuffle, warmup_rule=args.warmup_rule)
 
+    zero_src = [s for s in my_sources if deg[s] == 0]
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -791,23 +905,31 @@ def main():
                        "variant": variant_name(args),
                        "graph": "R-MAT scale 20, edge factor 16, "
                        "(0.57,0.19,0.19,0.05), dedup, no self-loops, seed %d" % GRAPH_SEED,
-                       "n": n, "m": m, "c": C, "eps": EPS, "sources": N_SOURCES,
+                       "n": n, "m": m, "c": C, "eps": EPS,
+                       "step": "one pass over all %d sources of the list, one query per "
+                               "launch" % n_src,
+                       "sources_per_step": n_src,
+                       "queries_timed_per_rank": args.steps * n_src,
+                       "sources_timed": my_sources,
+                       "sources_without_in_neighbours": len(zero_src),
                        "source_seed": SOURCE_SEED, "query_seed": QUERY_SEED,
-                       "adjacency": srk.srk_graph_layout(g),
+                       "adjacency": layout,
                        "z": stats_steps[0][4], "N_tot": stats_steps[0][2],
                        "L": int(stats_steps[0][5]),
                        "l2": "256 MB buffer written between queries (outside the timed intervals)",
                        "timing": "sum of per-query CUDA-event intervals on the query stream",
-                       "parallelism": "sources sharded over ranks" if world > 1 else "1 GPU"},
+                       "parallelism": "each rank runs its own 64-source list" if world > 1
+                       else "1 GPU"},
             "walk_steps_per_s": steps_per_s,
-            "target_steps_per_query": tgt_steps / args.steps,
+            "target_steps_per_query": tgt_steps / launches,
             "query_ms": {"best": float(np.min(q_ms)), "median": float(np.median(q_ms)),
                          "max": float(np.max(q_ms)),
                          "note": "per-query CUDA-event times on this rank; sources differ "
-                                 "in work (active pairs per target)"},
+                                 "in work (active pairs per target); a source without "
+                                 "in-neighbours returns after the source phases"},
             "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "e2e": e2e, "clocks": clk,
-            "gpu_launches": 9 * args.steps,
+            "gpu_launches": 9 * launches,
             "wall_s_timed_loop": t_wall, "graph_gen_s": t_gen}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -276,8 +276,10 @@ int srk_linear_ctx_free(srk_linear_ctx *ctx);
  *   the needed size otherwise).
  *   Scratch: one static device array of SRK_NOALLOC_SCRATCH_BYTES, held on
  *   every GPU where the library's module is loaded until the process exits.
- *   Its address is looked up by the first call on each device (make that
- *   first call before any stream capture).  Every call reuses the array and
+ *   Its address is looked up by the first call in each CUDA context of a
+ *   device (make that first call before any stream capture; a context that
+ *   replaced an earlier one, e.g. after cudaDeviceReset, gets a fresh
+ *   lookup).  Every call reuses the array and
  *   clears what must start at zero; calls that overlap on the GPU (e.g. on
  *   two streams) race on it and must be serialised by the caller.
  */
@@ -312,6 +314,21 @@ int srk_probe_gather(const int32_t *data, int64_t n, int64_t iters, uint32_t see
 int srk_probe_gather_ex(const int32_t *data, int64_t n, int64_t iters, uint32_t seed,
                         int32_t cache_op, unsigned long long *sink, int64_t *loads,
                         void *cuda_stream);
+
+/*
+ * srk_pool_stats -- what the library's stream-ordered memory pool of `device`
+ * holds (a measurement utility; the paper has no counterpart).  Queries take
+ * their scratch from this pool and return it when they finish.
+ *   reserved:  bytes of device memory backing the pool now;
+ *   used:      bytes handed out to queries in flight now;
+ *   used_high: the largest `used` since the pool was created or the mark was
+ *              last reset.
+ * Any output pointer may be NULL.  reset_high != 0 resets the mark to the
+ * current use after reading it.  SRK_EINVAL for a device outside
+ * [0, device count), SRK_ECUDA when the pool cannot be created or read.
+ */
+int srk_pool_stats(int32_t device, uint64_t *reserved, uint64_t *used, uint64_t *used_high,
+                   int reset_high);
 
 /*
  * Query server (no counterpart in the paper; the serving configuration):

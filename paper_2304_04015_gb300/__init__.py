@@ -27,7 +27,7 @@ __all__ = [
     "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free", "LinearContext",
     "LinearSimRank", "linear_simrank", "SrkServerReport", "Server",
     "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
-    "srk_server_destroy", "srk_last_error",
+    "srk_server_destroy", "srk_last_error", "srk_pool_stats",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
     "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_ADJ_NARROW", "SRK_ADJ_WIDE", "SRK_OPT_NO_GRAPH", "SRK_OPT_WARMUP_RULE", "SRK_OPT_LITERAL_SHUFFLE", "SRK_MAX_LEN",
@@ -114,8 +114,11 @@ _lib.srk_server_submit.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c
 _lib.srk_server_drain.argtypes = [_vp]
 _lib.srk_server_stats.argtypes = [_vp, ctypes.POINTER(SrkServerReport)]
 _lib.srk_server_destroy.argtypes = [_vp]
+_lib.srk_pool_stats.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
 _lib.srk_last_error.restype = ctypes.c_char_p
-for _f in ("srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout",
+for _f in ("srk_pool_stats", "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout",
            "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
            "srk_probe_gather", "srk_probe_gather_ex", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free",
            "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
@@ -380,6 +383,16 @@ class LinearContext:
             self.free()
         except Exception:
             pass
+
+
+def srk_pool_stats(device: int = 0, reset_high: bool = False):
+    """(reserved, used, used_high) bytes of the library's memory pool on
+    ``device`` (``srk_pool_stats``); ``reset_high`` resets the high-water
+    mark to the current use after reading it."""
+    r, u, h = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.srk_pool_stats(int(device), ctypes.byref(r), ctypes.byref(u), ctypes.byref(h),
+                               1 if reset_high else 0))
+    return r.value, u.value, h.value
 
 
 def srk_probe_gather_ex(data, iters: int, seed: int, cache_op: int, sink, stream=None) -> int:

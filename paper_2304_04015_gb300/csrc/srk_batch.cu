@@ -464,8 +464,12 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
   int rc = SRK_OK;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   if (use_graph) {
-    cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
+    cudaError_t e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (ev_in) cudaEventDestroy(ev_in);
+      return cuda_fail(e, "srk_multi_source: creating the graph-launch events");
+    }
   }
   while (i0 < k && rc == SRK_OK) {
     // sources [i0, i1) form this batch
@@ -575,9 +579,15 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     int shape = g->batch_cfg;
     if (shape < 0 || shape >= kNumShapes) {
       enqueue_source_side(st);
-      cudaEvent_t t0, t1;
-      cudaEventCreate(&t0);
-      cudaEventCreate(&t1);
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
+      e = cudaEventCreate(&t0);
+      if (e == cudaSuccess) e = cudaEventCreate(&t1);
+      if (e != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        rc = cuda_fail(e, "batched query: creating the autotuner's events");
+        cudaFreeAsync(base, st);
+        break;
+      }
       const int64_t trial = (int64_t)sms * 64 * 3;  // about three items per warp
       float best = 1e30f;
       shape = 0;

@@ -323,6 +323,32 @@ using namespace srk;
 
 extern "C" const char *srk_last_error(void) { return g_last_error.c_str(); }
 
+extern "C" int srk_pool_stats(int32_t device, uint64_t *reserved, uint64_t *used,
+                              uint64_t *used_high, int reset_high) {
+  clear_error();
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "srk_pool_stats: device count");
+  if (device < 0 || device >= count || device >= 64)
+    return fail(SRK_EINVAL, "device %d outside [0, %d)", device, count);
+  DeviceGuard guard(device);
+  cudaMemPool_t p = pool(device);
+  if (!p) return fail(SRK_ECUDA, "srk_pool_stats: cannot create the memory pool");
+  uint64_t r = 0, u = 0, h = 0;  // the attributes are 64-bit values
+  e = cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &r);
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &u);
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemHigh, &h);
+  if (e == cudaSuccess && reset_high) {
+    uint64_t zero = 0;  // resets the high-water mark to the current use
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrUsedMemHigh, &zero);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "srk_pool_stats");
+  if (reserved) *reserved = r;
+  if (used) *used = u;
+  if (used_high) *used_high = h;
+  return SRK_OK;
+}
+
 extern "C" int srk_graph_layout(const srk_graph *g, int32_t *layout) {
   if (!g || !layout) return fail(SRK_EINVAL, "null argument");
   *layout = g->layout == 1 ? SRK_ADJ_WIDE : g->layout == 2 ? SRK_ADJ_CSR : SRK_ADJ_NARROW;

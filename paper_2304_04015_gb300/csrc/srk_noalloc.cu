@@ -11,12 +11,16 @@
 //
 // The scratch is one file-scope __device__ array of SRK_NOALLOC_SCRATCH_BYTES.
 // It exists on every device on which this module is loaded, until the process
-// exits.  Its device address is looked up once per device with
-// cudaGetSymbolAddress, by the first call on that device (so that first call
-// should come before any stream capture).  All calls share the array and it
-// keeps the previous call's contents: every part a query needs zeroed is
-// cleared by the query itself, and calls whose work overlaps on the GPU (for
-// instance on two streams) race on it.
+// exits.  Its device address is looked up with cudaGetSymbolAddress by the
+// first call in each CUDA context (so that first call should come before any
+// stream capture); the address is kept per device together with the unique id
+// of the context it was taken in, and taken again when that context has been
+// replaced (after cudaDeviceReset, for instance).  All calls share the array
+// and it keeps the previous call's contents: every part a query needs zeroed
+// is cleared by the query itself, and calls whose work overlaps on the GPU
+// (for instance on two streams) race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "srk_internal.h"
@@ -28,21 +32,58 @@ namespace srk {
 namespace {
 
 std::mutex g_addr_mu;
-void *g_addr[64] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // the context the address belongs to (0: none yet)
+  void *addr;
+};
+ScratchAddr g_addr[64] = {};
 
-// Device address of the scratch array on `device` (the current device).
+// Unique id of the calling thread's current CUDA context (0 when there is
+// none), through the driver's cuCtxGetCurrent and cuCtxGetId, reached via the
+// runtime so that the library links no driver stub.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  using GetId = CUresult (*)(CUcontext, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(f1);
+      get_id = reinterpret_cast<GetId>(f2);
+    }
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on `device` (the current device), in
+// the current context.
 int scratch_address(int device, char **out) {
   if (device < 0 || device >= 64) return fail(SRK_EINVAL, "device %d out of range", device);
   std::lock_guard<std::mutex> lk(g_addr_mu);
-  if (!g_addr[device]) {
+  unsigned long long ctx = current_context_id();
+  ScratchAddr &a = g_addr[device];
+  if (!a.addr || ctx == 0 || ctx != a.ctx_id) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
                        "srk_single_source_noalloc: scratch address");
-    g_addr[device] = p;
+    a.addr = p;
+    a.ctx_id = ctx ? ctx : current_context_id();  // the lookup made the context current
   }
-  *out = static_cast<char *>(g_addr[device]);
+  *out = static_cast<char *>(a.addr);
   return SRK_OK;
 }
 

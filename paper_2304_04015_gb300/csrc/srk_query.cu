@@ -457,10 +457,14 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   // the active targets
   const size_t nr = (size_t)(u_end - u_begin);
   if (nr > 0) {
-    cudaMemsetAsync(o.scores + u_begin, 0, sizeof(double) * nr, st);
-    if (o.counts) cudaMemsetAsync(o.counts + u_begin, 0, sizeof(uint32_t) * nr, st);
-    if (o.wsums) cudaMemsetAsync(o.wsums + u_begin, 0, sizeof(unsigned long long) * nr, st);
-    if (o.steps) cudaMemsetAsync(o.steps + u_begin, 0, sizeof(uint32_t) * nr, st);
+    e = cudaMemsetAsync(o.scores + u_begin, 0, sizeof(double) * nr, st);
+    if (e == cudaSuccess && o.counts)
+      e = cudaMemsetAsync(o.counts + u_begin, 0, sizeof(uint32_t) * nr, st);
+    if (e == cudaSuccess && o.wsums)
+      e = cudaMemsetAsync(o.wsums + u_begin, 0, sizeof(unsigned long long) * nr, st);
+    if (e == cudaSuccess && o.steps)
+      e = cudaMemsetAsync(o.steps + u_begin, 0, sizeof(uint32_t) * nr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the outputs of the target range");
   }
   k_hit_table<<<gN, 256, 0, st>>>(t, w.sigma, w.seff, w.spos, w.small, w.pair_j,
                                   w.pair_w, w.Hc);

@@ -33,7 +33,9 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["unit"] == "queries/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    q = d["config"]["sources_per_step"]     # a step is one pass over the source list
+    assert q == 64
+    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 * q / d["value"]) < 1e-6 * d["ms_per_step"]
     assert d["config"]["workload"].startswith("rmat20")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1

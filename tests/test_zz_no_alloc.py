@@ -7,6 +7,9 @@ kernels with scratch taken from a static device array.  Its results must equal
 those of the allocating entry point bit for bit -- the tolerance every parity
 test here uses for counts, weight sums and scores -- on two calls in a row,
 the second of which finds the first call's leftovers in the shared scratch.
+It must also allocate nothing: across calls made after the first (which takes
+the scratch address), neither the library's memory pool (its high-water mark
+of memory handed out) nor the device's free memory may change.
 This file is collected last so that a stop-at-first-failure run has already
 run every other test.
 """
@@ -77,5 +80,35 @@ def test_no_alloc_rejects_what_it_cannot_hold(srk):
         with pytest.raises(srk.SrkError) as e:   # host outputs would need staging
             srk.srk_single_source_noalloc(g, 0, 0.6, 0.5, 1, np.empty(200))
         assert e.value.code == srk.SRK_EINVAL
+    finally:
+        g.close()
+
+
+def test_no_alloc_allocates_nothing(srk):
+    import torch
+    from srk_inputs import rmat_in_csr
+    dev = torch.device("cuda:0")
+    rp, col = rmat_in_csr(16, seed=1)
+    n = rp.size - 1
+    hub = int(np.argmax(np.diff(rp)))
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        outs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in range(2)]
+        counts = torch.empty(n, dtype=torch.int32, device=dev)
+        # the first call in this context looks up the scratch address (and
+        # loads the kernels): set-up, outside the measured calls
+        srk.srk_single_source_noalloc(g, hub, 0.6, 0.05, 1, outs[0], counts)
+        torch.cuda.synchronize()
+        _, used0, _ = srk.srk_pool_stats(0, reset_high=True)
+        free0, _ = torch.cuda.mem_get_info(dev)
+        for k, seed in enumerate((2, 3)):
+            srk.srk_single_source_noalloc(g, hub, 0.6, 0.05, seed, outs[k], counts)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(dev)
+        _, used1, high1 = srk.srk_pool_stats(0)
+        assert high1 == used0 and used1 == used0     # no pool allocation in the calls
+        assert free1 == free0                        # and no other device allocation
+        assert not torch.equal(outs[0], outs[1])     # two different queries ran
+        assert int(counts.sum()) > 0
     finally:
         g.close()
