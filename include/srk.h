@@ -63,10 +63,15 @@ extern "C" {
                                   p and q are then not used */
 #define SRK_OPT_LITERAL_SHUFFLE 4  /* single-source only: shuffle every
                                   target's walks too, by a keyed per-target
-                                  permutation (unbalanced 4-round Feistel
+                                  permutation pi_u (unbalanced 4-round Feistel
                                   with hash round functions), as Section 5.2
-                                  shuffles every node's walks; about 3.6x
-                                  slower than the default pairing */
+                                  shuffles every node's walks.  Per target the
+                                  pairing stays a uniform bijection (the
+                                  source's shuffle is uniform); pi_u is only
+                                  pseudo-random, so the independence of the
+                                  pairings across targets that Section 5.2
+                                  has is approximated, not reproduced.  About
+                                  3.6x slower than the default pairing */
 
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */

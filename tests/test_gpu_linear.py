@@ -7,7 +7,10 @@ c=0.6, D=(1-c)I, loss = sum_v w_v s(s, v), w ~ N(0, 1)).
 
 Tolerances (FP32 arithmetic, FP64 references): forward
 |d| <= 1e-5 |ref| + 1e-7 max|ref|; gradient |d| <= 1e-4 |ref| + 1e-4 rms(ref)
-per edge.
+per edge, and normwise ||d|| <= 1e-4 ||ref|| over all checked edges (the
+relative error of 1e-4 the differentiable form is held to).  The R-MAT 18
+test also prints the realised normwise error and the worst per-edge relative
+error over the edges whose gradient is at least 1e-2 rms(ref).
 """
 import functools
 
@@ -56,9 +59,17 @@ def check_forward(got, ref):
 
 
 def check_grad(got, ref):
+    """Per-edge mixed bound and normwise relative bound; returns (normwise
+    relative error, worst relative error over edges with |ref| >= 1e-2 rms)."""
     rms = np.sqrt(np.mean(ref ** 2))
     tol = 1e-4 * np.abs(ref) + 1e-4 * rms
-    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+    d = got - ref
+    assert np.all(np.abs(d) <= tol), float(np.max(np.abs(d) / tol))
+    normwise = float(np.linalg.norm(d) / np.linalg.norm(ref))
+    assert normwise <= 1e-4, normwise
+    big = np.abs(ref) >= 1e-2 * rms
+    worst = float(np.max(np.abs(d[big]) / np.abs(ref[big]))) if big.any() else 0.0
+    return normwise, worst
 
 
 def test_small_graph_against_reverse_mode_oracle(srk):
@@ -85,12 +96,16 @@ def test_rmat18_configuration_gradients(srk):
     w64 = w.astype(np.float64)
     ref_g, ref_s = linear.grad(rp, col, w64, n, s, C, 10, g)
     check_forward(out, ref_s)
-    check_grad(gr, ref_g)
+    nw, worst = check_grad(gr, ref_g)
     # FP64 central finite differences on 256 sampled edges
     rng = np.random.default_rng(7)
     edges = rng.choice(col.size, 256, replace=False)
     fd = linear.finite_difference_pool(rp, col, w64, n, s, C, 10, g, edges)
-    check_grad(gr[edges], fd)
+    nw_fd, worst_fd = check_grad(gr[edges], fd)
+    print("linear gradient, R-MAT 18, L = 10: reverse-mode oracle on all %d edges: normwise "
+          "relative error %.3g, worst per-edge relative error (|ref| >= 1e-2 rms) %.3g; "
+          "finite differences on 256 edges: normwise %.3g, worst %.3g"
+          % (col.size, nw, worst, nw_fd, worst_fd))
     # scaling invariance of each in-list (P is unchanged): exact for the
     # oracle, and for the FP32 gradient within the per-edge tolerance above
     a_of_e = np.repeat(np.arange(n), deg)

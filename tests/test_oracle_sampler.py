@@ -135,6 +135,39 @@ def test_literal_shuffle_permutation_and_marginal():
     assert float(((counts - exp) ** 2 / exp).sum()) < 35.0
 
 
+def test_literal_shuffle_pairing_law_per_target_and_across_targets():
+    """Section 5.2 shuffles every node's walks independently, so target u's
+    walk t is paired with a uniformly random source walk, independently of
+    the other targets.  In the literal mode pair j joins source walk sigma(j)
+    (sigma: the source's uniform Fisher-Yates shuffle) and target walk
+    pi_u(j), so target walk t meets source walk sigma(pi_u^-1(t)).  Per target
+    that composition is a uniform bijection whatever pi_u is: over seeds, its
+    law on the 4! pairings of N = 4 walks passes a chi-square test (23 dof,
+    critical value 49.7 at p = 1e-3).  pi_u itself, a keyed 4-round Feistel
+    network, is only a pseudo-random bijection: on N = 4 its law over seeds
+    is far from uniform (chi-square well above the critical value), so the
+    independence across targets that Section 5.2 has is approximated, not
+    reproduced; Theorem 6 needs only the per-target law."""
+    import itertools
+    N, K = 4, 4800
+    perms = list(itertools.permutations(range(N)))
+    composed = dict.fromkeys(perms, 0)
+    feistel = dict.fromkeys(perms, 0)
+    for seed in range(K):
+        sigma = sampler.fisher_yates(7, seed, N)
+        pi = [sampler.feistel(11, 7, seed, N, j) for j in range(N)]
+        inv = [0] * N
+        for j, t in enumerate(pi):
+            inv[t] = j
+        composed[tuple(int(sigma[inv[t]]) for t in range(N))] += 1
+        feistel[tuple(pi)] += 1
+    exp = K / len(perms)
+    chi_composed = sum((c - exp) ** 2 / exp for c in composed.values())
+    chi_feistel = sum((c - exp) ** 2 / exp for c in feistel.values())
+    assert chi_composed < 49.7
+    assert chi_feistel > 49.7
+
+
 @pytest.mark.parametrize("n,deg,s,seed", [(60, 3.0, 0, 11), (50, 2.0, 9, 4)])
 def test_literal_shuffle_algorithm2_equals_direct(n, deg, s, seed):
     rp, col = er_in_csr(n, deg, seed=seed)
