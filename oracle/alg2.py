@@ -35,10 +35,11 @@ def tuples_of_walk(j: int, walk_nodes, length: int, v0: int):
 
 
 def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
-        z_override=None, L_override=None, literal_shuffle=False):
+        z_override=None, L_override=None, literal_shuffle=False, shared_walks=False):
     """``literal_shuffle``: every target's walk r carries the label j with
     pi_u(j) = r (the keyed per-target permutation), as the paper shuffles
-    every node's walks."""
+    every node's walks.  ``shared_walks``: the other nodes' walks are drawn
+    with the shared key (the same walks for every source)."""
     tab = sample_table(n, c, eps, z_override=z_override, L_override=L_override)
     L, N_tot = tab.L, tab.N_tot
     lengths = np.array([tab.stratum(r) for r in range(N_tot)], dtype=np.int64)
@@ -48,7 +49,8 @@ def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
 
     J, I, V, T, V0 = [], [], [], [], []
     for v0 in range(n):
-        pos, eff = sampler.walks(row_ptr, col, v0, s, seed, tab)
+        key = sampler.SHARED_KEY if shared_walks and v0 != s else s
+        pos, eff = sampler.walks(row_ptr, col, v0, key, seed, tab)
         inv_u = None
         if literal_shuffle and v0 != s:
             inv_u = np.empty(N_tot, dtype=np.int64)

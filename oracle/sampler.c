@@ -32,6 +32,12 @@
  *           words 2*(t&1) (high) and 2*(t&1)+1 (low)
  *   uniform index below d from a 64-bit draw R: floor(R * d / 2^64).
  *
+ * Optional shared target walks (Algorithm 1 draws every node's walks once,
+ * whatever the query): walk r of a target v is then keyed by (v, r) alone,
+ * counter ((i-1) >> 1, r, v, 0xFFFFFFFE), so the walks of v are the same for
+ * every source and a batch of sources can share them.  Source walks keep the
+ * counter ((i-1) >> 1, r, s, s) (s < 2^31, so the two never coincide).
+ *
  * Optional literal shuffle of the targets' walks (every node's walks are
  * shuffled in Section 5.2; the default shuffles only the source's): target u
  * pairs walk pi_u(j) with source walk sigma[j], where pi_u is a keyed
@@ -97,6 +103,9 @@ static uint64_t draw64(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
     srko_philox4x32_10(ctr, key, w);
     return ((uint64_t)w[2 * half] << 32) | w[2 * half + 1];
 }
+
+/* Counter word of the shared target walks, as a signed 32-bit value. */
+#define SRKO_SHARED_KEY ((int32_t)-2)
 
 /* One walk of nominal length `len` from v, replica r, query source s.
  * Writes the node at step i to pos[i-1]; returns the number of steps taken
@@ -205,7 +214,8 @@ void srko_fisher_yates(int32_t s, uint64_t seed, int32_t N_tot,
 
 /*
  * Steps a2-a4 for query source s and the targets listed in `targets`
- * (literal != 0: target walks are paired through pi_u, see above)
+ * (literal != 0: target walks are paired through pi_u, see above; shared != 0:
+ * target walks take the shared key, see above)
  * (n_targets entries; any node ids, s included).  wq is the (L+1)x(L+1)
  * quantised weight table, row l1 (source length), column l2 (target length).
  * Outputs per listed target: meet count, weight sum (2^-32 units) and the
@@ -218,7 +228,7 @@ int srko_sampler(const int32_t *row_ptr, const int32_t *col, int32_t n,
                  const uint64_t *wq, const int32_t *targets,
                  int64_t n_targets, uint32_t *count, uint64_t *wsum,
                  uint64_t *steps, uint64_t *source_steps, int threads,
-                 int literal) {
+                 int literal, int shared) {
     (void)n;
     int stride = L > 0 ? L : 1;
     int32_t N_tot = P[L + 1];
@@ -267,7 +277,8 @@ int srko_sampler(const int32_t *row_ptr, const int32_t *col, int32_t n,
                     int l2 = stratum_of(P, L, tw);
                     int32_t w = sigma[j];
                     int l1 = stratum_of(P, L, w);
-                    int teff = srko_walk(row_ptr, col, u, tw, s, seed, l2, tpos);
+                    int teff = srko_walk(row_ptr, col, u, tw, shared ? SRKO_SHARED_KEY : s,
+                                         seed, l2, tpos);
                     int m = teff < seff[w] ? teff : seff[w];
                     const int32_t *sp = spos + (int64_t)w * stride;
                     int met = 0;

@@ -58,7 +58,7 @@ def lib():
         L.srko_sampler.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_uint64, ctypes.c_int, i32p, u64p,
                                    i32p, ctypes.c_int64, u32p, u64p, u64p, u64p,
-                                   ctypes.c_int, ctypes.c_int]
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.srko_sampler.restype = ctypes.c_int
         L.srko_feistel.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                    ctypes.c_int32, ctypes.c_int32]
@@ -82,6 +82,10 @@ def philox4x32_10(ctr, key):
 
 def index(r: int, d: int) -> int:
     return int(lib().srko_index(ctypes.c_uint64(r), ctypes.c_uint32(d)))
+
+
+# Counter word that keys the shared target walks in place of the source.
+SHARED_KEY = -2
 
 
 def walk(row_ptr, col, v: int, r: int, s: int, seed: int, length: int):
@@ -144,9 +148,11 @@ class Result:
 def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
         targets=None, z_override=None, L_override=None, p: float = 1.0,
         q: float = 1.0, warmup_rule: bool = False, literal_shuffle: bool = False,
-        threads: int = 0) -> Result:
+        shared_walks: bool = False, threads: int = 0) -> Result:
     """One single-source query, steps a1-a5, for ``targets`` (all nodes if None).
-    ``literal_shuffle``: also shuffle every target's walks (by pi_u)."""
+    ``literal_shuffle``: also shuffle every target's walks (by pi_u).
+    ``shared_walks``: target walks keyed by (node, replica) alone, the same for
+    every source (``SHARED_KEY``)."""
     tab = sample_table(n, c, eps, p=p, q=q, z_override=z_override,
                        L_override=L_override, warmup_rule=warmup_rule)
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -169,7 +175,7 @@ def run(row_ptr, col, n: int, s: int, c: float, eps: float, seed: int, *,
                             _ptr(wsum, ctypes.c_uint64),
                             _ptr(steps, ctypes.c_uint64),
                             _ptr(src_steps, ctypes.c_uint64), threads,
-                            1 if literal_shuffle else 0)
+                            1 if literal_shuffle else 0, 1 if shared_walks else 0)
     if rc != 0:
         raise MemoryError("oracle sampler ran out of memory")
     # a5: s~(s, u) = W_u 2^-32 / z; s~(s, s) = 1

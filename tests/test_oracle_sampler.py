@@ -8,6 +8,9 @@
 * Unbiasedness: the mean over many seeds equals the exact expectation of the
   estimator (first-meeting recursion) within a CLT band.
 * Step totals against a plain re-walk of each pair.
+* Shared target walks (keyed by node and replica alone, as Algorithm 1 draws
+  every node's walks once): the literal Algorithm 2 path, the mean over seeds
+  against the exact expectation, and walks that no longer depend on s.
 """
 import numpy as np
 import pytest
@@ -95,6 +98,45 @@ def test_mean_over_seeds_matches_exact_expectation():
     assert zscore.max() < 5.0
     # where no pair can ever meet, the estimate is exactly zero
     assert np.all(mean[expect == 0.0] == 0.0)
+
+
+@pytest.mark.parametrize("n,deg,s,seed", [(60, 3.0, 0, 11), (50, 2.0, 9, 4)])
+def test_shared_walks_algorithm2_equals_direct(n, deg, s, seed):
+    rp, col = er_in_csr(n, deg, seed=seed)
+    r = sampler.run(rp, col, n, s, C, 0.5, seed, z_override=300.0, shared_walks=True)
+    cnt, ws = alg2.run(rp, col, n, s, C, 0.5, seed, z_override=300.0, shared_walks=True)
+    assert np.array_equal(r.count, cnt) and np.array_equal(r.wsum, ws)
+    plain = sampler.run(rp, col, n, s, C, 0.5, seed, z_override=300.0)
+    assert not np.array_equal(plain.count, r.count)     # the keying changed the walks
+
+
+def test_shared_walks_do_not_depend_on_the_source():
+    rp, col = er_in_csr(60, 3.0, seed=3)
+    for v, r in ((5, 0), (17, 33), (42, 7)):
+        a = sampler.walk(rp, col, v, r, sampler.SHARED_KEY, 9, 20)
+        assert a.size > 0
+        for s in (0, 1, 59):   # a source walk from v is keyed by s instead
+            assert not np.array_equal(a, sampler.walk(rp, col, v, r, s, 9, 20)) or v == s
+
+
+def test_shared_walks_mean_matches_exact_expectation():
+    # shared target walks leave each (s, u) estimate's law unchanged
+    n, s = 120, 0
+    rp, col = er_in_csr(n, 2.0, seed=21)
+    tab = sample_table(n, C, 0.5, z_override=300.0, L_override=15)
+    F = exact.first_meeting(rp, col, n, tab.L, rows=[s])[:, 0, :]
+    expect = exact.estimator_expectation(F, tab, quantised=True)
+    seeds = 300
+    acc = np.zeros((seeds, n))
+    for k in range(seeds):
+        acc[k] = sampler.run(rp, col, n, s, C, 0.5, 7000 + k, z_override=300.0,
+                             L_override=15, shared_walks=True).scores
+    acc[:, s] = 0.0
+    expect[s] = 0.0
+    mean, sd = acc.mean(axis=0), acc.std(axis=0, ddof=1)
+    live = sd > 0
+    z = np.abs(mean[live] - expect[live]) / (sd[live] / np.sqrt(seeds))
+    assert live.sum() > 10 and z.max() < 5.0
 
 
 def test_step_totals_against_plain_rewalk():
