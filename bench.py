@@ -87,6 +87,10 @@ def parse():
                     help="serve: latency target of the admission (0: memory only, FIFO)")
     ap.add_argument("--batch-sources", type=int, default=12,
                     help="sources of the 4096-source batching list that are run")
+    ap.add_argument("--shared-walks", action="store_true",
+                    help="batch: target walks drawn once for all sources of a batch "
+                         "(SRK_OPT_SHARED_WALKS), against one query per launch with the "
+                         "same flag")
     return ap.parse_args()
 
 
@@ -337,20 +341,25 @@ def run_batch(args, rank, world):
     k = len(sources)
     out = torch.empty((k, n), dtype=torch.float64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sw = args.shared_walks
     # warm-up: the first call autotunes the persistent kernel's launch shape
-    srk.srk_multi_source(g, sources[:3], C, eps[:3], QUERY_SEED, out[:3])
+    srk.srk_multi_source(g, sources[:3], C, eps[:3], QUERY_SEED, out[:3], shared_walks=sw)
     torch.cuda.synchronize()
     st = srk.SrkStats()
     ev[0].record()
-    srk.srk_multi_source(g, sources, C, eps, QUERY_SEED, out, stats=st)
+    srk.srk_multi_source(g, sources, C, eps, QUERY_SEED, out, stats=st, shared_walks=sw)
     ev[1].record()
     ev[1].synchronize()
     t_batch = ev[0].elapsed_time(ev[1]) / 1e3
     single = torch.empty(n, dtype=torch.float64, device=dev)
-    t_plain, same = 0.0, True
+    t_plain, same, plain_steps = 0.0, True, 0
     for i, s in enumerate(sources):
+        pst = srk.SrkStats()
+        srk.srk_single_source(g, s, C, eps[i], QUERY_SEED, single, stats=pst, shared_walks=sw)
+        plain_steps += pst.target_steps
+        torch.cuda.synchronize()
         ev[0].record()
-        srk.srk_single_source(g, s, C, eps[i], QUERY_SEED, single)
+        srk.srk_single_source(g, s, C, eps[i], QUERY_SEED, single, shared_walks=sw)
         ev[1].record()
         ev[1].synchronize()
         t_plain += ev[0].elapsed_time(ev[1]) / 1e3
@@ -374,7 +383,9 @@ def run_batch(args, rank, world):
         base = cpu_baseline_mix([(rp, col_h)], mix, args.cpu_seconds)
         del col_h
     line = {"metric": "batched multi-source queries/s (R-MAT scale %d, mixed eps)" % args.batch_scale,
-            "workload": "batch_rmat%d_mixed_sources_mixed_eps" % args.batch_scale,
+            "workload": "batch_rmat%d_mixed_sources_mixed_eps%s" % (args.batch_scale,
+                                                                   "_shared_walks" if sw else ""),
+            "shared_walks": sw, "plain_target_steps": plain_steps,
             "value": k / t_batch, "unit": "queries/s", "higher_is_better": True,
             "plain_value": k / t_plain, "batched_over_plain": t_plain / t_batch,
             "identical_to_plain": same, "sources": k, "n": n, "m": m,

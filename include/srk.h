@@ -73,6 +73,19 @@ extern "C" {
                                   has is approximated, not reproduced.  About
                                   3.6x slower than the default pairing */
 
+#define SRK_OPT_SHARED_WALKS 8  /* target walks keyed by (node, replica) alone:
+                                  walk r of target u draws step i from the
+                                  Philox counter ((i-1)>>1, r, u, 0xFFFFFFFE)
+                                  instead of ((i-1)>>1, r, u, s), so every
+                                  node's walks are the same for all sources,
+                                  as Algorithm 1 draws each node's walks once.
+                                  Each (s, u) estimate keeps its law; estimates
+                                  of different sources share target walks.
+                                  srk_multi_source then walks each target once
+                                  for all sources of a batch (up to 32 at a
+                                  time); its results equal those of
+                                  srk_single_source with this flag */
+
 /* srk_graph_load flags. */
 #define SRK_DEVICE_PTRS 1  /* row_ptr/col/edge_w are device pointers, borrowed */
 #define SRK_VALIDATE    2  /* accepted; the CSR invariants are always checked */

@@ -30,13 +30,13 @@ __all__ = [
     "srk_server_destroy", "srk_last_error", "srk_pool_stats",
     "library_path", "SRK_NOALLOC_SCRATCH_BYTES",
     "SRK_OK", "SRK_EINVAL", "SRK_ENOMEM", "SRK_ECUDA", "SRK_ETIMEOUT",
-    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_ADJ_NARROW", "SRK_ADJ_WIDE", "SRK_OPT_NO_GRAPH", "SRK_OPT_WARMUP_RULE", "SRK_OPT_LITERAL_SHUFFLE", "SRK_MAX_LEN",
+    "SRK_ENOTSUP", "SRK_DEVICE_PTRS", "SRK_VALIDATE", "SRK_ADJ_NARROW", "SRK_ADJ_WIDE", "SRK_OPT_NO_GRAPH", "SRK_OPT_WARMUP_RULE", "SRK_OPT_LITERAL_SHUFFLE", "SRK_OPT_SHARED_WALKS", "SRK_MAX_LEN",
     "SRK_MAX_WALKS",
 ]
 
 SRK_OK, SRK_EINVAL, SRK_ENOMEM, SRK_ECUDA, SRK_ETIMEOUT, SRK_ENOTSUP = 0, -1, -2, -3, -4, -5
 SRK_DEVICE_PTRS, SRK_VALIDATE, SRK_ADJ_NARROW, SRK_ADJ_WIDE, SRK_ADJ_CSR = 1, 2, 4, 8, 16
-SRK_OPT_NO_GRAPH, SRK_OPT_WARMUP_RULE, SRK_OPT_LITERAL_SHUFFLE = 1, 2, 4
+SRK_OPT_NO_GRAPH, SRK_OPT_WARMUP_RULE, SRK_OPT_LITERAL_SHUFFLE, SRK_OPT_SHARED_WALKS = 1, 2, 4, 8
 SRK_PROBE_DEFAULT, SRK_PROBE_CG, SRK_PROBE_NC, SRK_PROBE_CA = 0, 1, 2, 3
 SRK_MAX_LEN, SRK_MAX_WALKS = 255, 1 << 24
 SRK_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -248,10 +248,13 @@ def srk_graph_info(g: Graph):
 
 def _opts(z_override=None, L_override=None, p=None, q=None, step_counts=None,
           stats: Optional[SrkStats] = None, timing_events=None, flags: int = 0,
-          target_range=None, warmup_rule: bool = False, literal_shuffle: bool = False):
+          target_range=None, warmup_rule: bool = False, literal_shuffle: bool = False,
+          shared_walks: bool = False):
     o = SrkOpts()
     if literal_shuffle:
         flags |= SRK_OPT_LITERAL_SHUFFLE
+    if shared_walks:
+        flags |= SRK_OPT_SHARED_WALKS
     if target_range is not None:
         o.target_begin, o.target_end = int(target_range[0]), int(target_range[1])
     if warmup_rule:
@@ -278,7 +281,8 @@ def srk_single_source(g: Graph, s: int, c: float, eps: float, seed: int,
                       z_override=None, L_override=None, p=None, q=None,
                       step_counts=None, stats: Optional[SrkStats] = None,
                       timing_events=None, target_range=None, warmup_rule: bool = False,
-                      literal_shuffle: bool = False, stream=None) -> None:
+                      literal_shuffle: bool = False, shared_walks: bool = False,
+                      stream=None) -> None:
     """One query (``srk_single_source``): fills ``scores`` (n float64) and,
     when given, ``meet_counts`` (n uint32), ``weight_sums`` (n uint64),
     ``step_counts`` (n uint32) and ``stats``.  ``timing_events``: two
@@ -289,7 +293,7 @@ def srk_single_source(g: Graph, s: int, c: float, eps: float, seed: int,
     ws, _, k3 = _ptr(weight_sums, "uint64")
     o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events,
                   target_range=target_range, warmup_rule=warmup_rule,
-                  literal_shuffle=literal_shuffle)
+                  literal_shuffle=literal_shuffle, shared_walks=shared_walks)
     rc = _lib.srk_single_source(g.handle, int(s), float(c), float(eps),
                                 int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                                 sc, mc, ws, _stream_handle(stream))
@@ -303,7 +307,7 @@ def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
                               step_counts=None, stats: Optional[SrkStats] = None,
                               timing_events=None, target_range=None,
                               warmup_rule: bool = False, literal_shuffle: bool = False,
-                              stream=None) -> None:
+                              shared_walks: bool = False, stream=None) -> None:
     """``srk_single_source`` for callers that must not allocate device memory
     while querying: the scratch is a static device array of
     ``SRK_NOALLOC_SCRATCH_BYTES``; outputs must be device tensors; calls that
@@ -313,7 +317,7 @@ def srk_single_source_noalloc(g: Graph, s: int, c: float, eps: float, seed: int,
     ws, _, k3 = _ptr(weight_sums, "uint64")
     o, k4 = _opts(z_override, L_override, p, q, step_counts, stats, timing_events,
                   target_range=target_range, warmup_rule=warmup_rule,
-                  literal_shuffle=literal_shuffle)
+                  literal_shuffle=literal_shuffle, shared_walks=shared_walks)
     rc = _lib.srk_single_source_noalloc(g.handle, int(s), float(c), float(eps),
                                         int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o),
                                         sc, mc, ws, _stream_handle(stream))
@@ -325,12 +329,14 @@ def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
                      meet_counts=None, *, z_override=None, L_override=None,
                      p=None, q=None, stats: Optional[SrkStats] = None,
                      no_graph: bool = False, warmup_rule: bool = False,
-                     literal_shuffle: bool = False, stream=None) -> None:
+                     literal_shuffle: bool = False, shared_walks: bool = False,
+                     stream=None) -> None:
     """k queries (``srk_multi_source``): ``sources`` and ``eps`` are host
     sequences of length k; ``scores`` is k x n float64.  ``no_graph``: enqueue
     the batch launches directly instead of through a captured CUDA graph.
-    ``literal_shuffle`` is passed through and rejected by the library (the
-    batched path runs the plain mode only)."""
+    ``shared_walks``: every target's walks are drawn once for all sources of
+    a batch (``SRK_OPT_SHARED_WALKS``).  ``literal_shuffle`` is passed through
+    and rejected by the library."""
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
     k = src.size
     eps_a = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (k,)))
@@ -338,7 +344,7 @@ def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
     mc, _, k2 = _ptr(meet_counts, "uint32")
     o, _ = _opts(z_override, L_override, p, q, None, stats,
                  flags=SRK_OPT_NO_GRAPH if no_graph else 0, warmup_rule=warmup_rule,
-                 literal_shuffle=literal_shuffle)
+                 literal_shuffle=literal_shuffle, shared_walks=shared_walks)
     rc = _lib.srk_multi_source(g.handle, src.ctypes.data, k, float(c), eps_a.ctypes.data,
                                int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), sc, mc,
                                _stream_handle(stream))

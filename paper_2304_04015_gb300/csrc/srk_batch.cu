@@ -34,6 +34,9 @@ struct BatchSrc {
   double *scores;         // output row, n entries
   uint32_t *counts;       // output row or null
   unsigned long long *steps;  // target-walk steps of this source (one counter)
+  int32_t *Hj;                // shared walks: node of source walk sigma(j) at step i,
+                              // at Hj[(i-1) N_tot + j] for i <= cap(j)
+  unsigned long long *wj;     // shared walks: quantised Lemma 7 weight of pair j
   int32_t s, L, N_tot;
   double z;
 };
@@ -49,6 +52,9 @@ struct BatchArgs {
   const int32_t *npos;
   int32_t pos_bits;
   uint32_t key0, key1;
+  uint32_t *M;    // shared walks: bit b of M[(i-1) Jmax + j] = pair j of batch
+                  // source b may still meet at step i (cap_b(j) >= i); Lmax + 1 rows
+  int32_t Jmax;   // shared walks: the largest N_tot of the batch
 };
 
 __device__ __forceinline__ int find_source(const int64_t *off, int k, int64_t g) {
@@ -313,6 +319,170 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   if (lane == 0 && cur >= 0 && acc) atomicAdd(A.src[cur].steps, acc);
 }
 
+// ------------------------------------------------------------------------
+// Shared target walks (SRK_OPT_SHARED_WALKS).  Target walk j of u no longer
+// depends on the source, so one walk serves pair j of every source of the
+// batch: it goes on while some source's pair j can still meet (it has not met
+// and its cap is not reached) and stops at a node without in-neighbours.  For
+// source b the pair meets at the first step i <= cap_b(j) where the walk is
+// at Hj_b[(i-1) N_b + j], exactly as srk_single_source with the same flag
+// decides it.  Batches hold at most 32 sources (one mask bit each).
+
+// Per source and pair j: the pair's weight, its hit-table column (steps
+// 1..cap(j) of source walk sigma(j)) and its bit in the step masks.
+__global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
+  SRK_BATCH_LOOP(A, {
+    const int32_t j = r_;
+    const int32_t w = S_.w.sigma[j];
+    const int l2 = stratum_of(S_.tab->P, S_.L, j);
+    const int32_t cap = min(l2, S_.w.seff[w]);
+    const int l1 = stratum_of(S_.tab->P, S_.L, w);
+    S_.wj[j] = cap >= 1 ? __double2ull_rn(S_.tab->a[l1] * S_.tab->a[l2] * 4294967296.0) : 0ull;
+    const int Ls = S_.L > 0 ? S_.L : 1;
+    const int32_t *sp = S_.w.spos + (int64_t)w * Ls;
+    const uint32_t bit = 1u << i_;
+    for (int q = 1; q <= cap; ++q) {
+      S_.Hj[(int64_t)(q - 1) * S_.N_tot + j] = sp[q - 1];
+      atomicOr(&A.M[(int64_t)(q - 1) * A.Jmax + j], bit);
+    }
+  })
+}
+
+// The batch's sources as the shared-walk kernel reads them (shared memory).
+struct ShSrc {
+  const int32_t *Hj;
+  const unsigned long long *wj;
+  double *scores;
+  uint32_t *counts;
+  double z;
+  int32_t N, s;
+};
+
+// Meetings at step i of walk j (node x) for the sources in `pend`: each
+// source whose hit-table entry equals x counts the pair once (count and
+// weight into the warp's accumulators) and leaves `pend`.
+__device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, uint32_t pend, int i, int32_t j,
+                                                int32_t x, uint32_t *cnt,
+                                                unsigned long long *wsum) {
+  for (uint32_t m = pend; m; m &= m - 1) {
+    const int b = __ffs(m) - 1;
+    const ShSrc &S = src[b];
+    if (S.Hj[(int64_t)(i - 1) * S.N + j] == x) {
+      atomicAdd(&cnt[b], 1u);
+      atomicAdd(&wsum[b], S.wj[j]);
+      pend &= ~(1u << b);
+    }
+  }
+  return pend;
+}
+
+// a4+a5 of a batch with shared target walks: warps take targets (the nodes
+// with in-neighbours) from a counter; the 32 lanes walk the target's pairs
+// j = j0, j0 + 1, ... with lane refill, one Philox block (counter
+// ((i-1)>>1, j, u, kSharedWalkKey)) per odd and following even step; per
+// source the warp accumulates meetings in shared memory and writes count and
+// score at the end of the target.  A source's own row keeps its prefilled 1.
+template <int kLayout>
+__global__ void __launch_bounds__(256, 6)
+kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
+                int32_t n_act, int32_t j0, unsigned long long *__restrict__ ctr) {
+  __shared__ ShSrc src[32];
+  __shared__ uint32_t cnt[8][32];
+  __shared__ unsigned long long wsum[8][32];
+  for (int b = threadIdx.x; b < A.k; b += blockDim.x) {
+    const BatchSrc &B = A.src[b];
+    src[b] = ShSrc{B.Hj, B.wj, B.scores, B.counts, B.z, B.N_tot, B.s};
+  }
+  __syncthreads();
+  const RoundKeys rk = round_keys(A.key0, A.key1);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t lanes_below = (1u << lane) - 1u;
+  const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
+  const uint32_t *M = A.M;
+  const int32_t J = A.Jmax;
+  unsigned long long warp_steps = 0;
+  for (;;) {
+    int32_t q = 0;
+    if (lane == 0) q = (int32_t)atomicAdd(ctr, 1ull);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= n_act) break;
+    const uint32_t u = (uint32_t)act[q];
+    // sources whose own row this target is
+    const uint32_t excl = __ballot_sync(0xffffffffu, lane < A.k && src[lane].s == (int32_t)u);
+    if (lane < A.k) {
+      cnt[wib][lane] = 0u;
+      wsum[wib][lane] = 0ull;
+    }
+    __syncwarp();
+    uint32_t deg_u = 0;
+    const int32_t b_u = node_start(G, A.row_ptr, (int32_t)u, deg_u);
+    uint32_t st = 0;
+    int32_t next = j0, j = 0, i = 1, b = 0;
+    bool live = false;
+    uint32_t deg = 0, pend = 0;
+    for (;;) {
+      const uint32_t idle = __ballot_sync(0xffffffffu, !live);
+      if (idle) {
+        if (!live) {
+          j = next + __popc(idle & lanes_below);
+          if (j < J) {
+            pend = M[j] & ~excl;
+            live = pend != 0u;
+            i = 1;
+            b = b_u;
+            deg = deg_u;
+          }
+        }
+        next += __popc(idle);
+      }
+      if (!__any_sync(0xffffffffu, live)) {
+        if (next >= J) break;
+        continue;  // every pair of this round was dead: take the next ones
+      }
+      if (live) {
+        uint32_t x0, x1, x2, x3;
+        philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)j, u, kSharedWalkKey, x0, x1, x2, x3);
+        auto e = adj_entry(G, b, deg, x0, x1);  // odd step i
+        int32_t x = entry_pos(G, e);
+        ++st;
+        pend = shared_meet(src, pend, i, j, x, cnt[wib], wsum[wib]);
+        pend &= M[(int64_t)i * J + j];  // still able to meet at step i + 1
+        if (!pend) {
+          live = false;
+        } else {
+          b = entry_next(G, e, x, deg);
+          if (deg == 0) {
+            live = false;
+          } else {
+            e = adj_entry(G, b, deg, x2, x3);  // even step i + 1
+            x = entry_pos(G, e);
+            ++st;
+            pend = shared_meet(src, pend, i + 1, j, x, cnt[wib], wsum[wib]);
+            pend &= M[(int64_t)(i + 1) * J + j];
+            if (!pend) {
+              live = false;
+            } else {
+              b = entry_next(G, e, x, deg);
+              if (deg == 0) live = false;
+              i += 2;
+            }
+          }
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(0xffffffffu, st, off);
+    warp_steps += st;
+    __syncwarp();
+    if (lane < A.k && !((excl >> lane) & 1u)) {
+      const ShSrc &S = src[lane];
+      S.scores[u] = (double)wsum[wib][lane] * 2.3283064365386963e-10 / S.z;
+      if (S.counts) S.counts[u] = cnt[wib][lane];
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && warp_steps) atomicAdd(ctr + 1, warp_steps);
+}
+
 // The candidate launch shapes of the autotuner (block size, blocks per SM).
 struct Shape {
   int block, per_sm;
@@ -392,6 +562,32 @@ static void launch_targets(int layout, int shape, int sms, cudaStream_t st, cons
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The shared-walk kernel: a persistent grid of as many 256-thread blocks as
+// fit at once (ctr[0]: the target counter, cleared here; ctr[1]: the steps).
+static void launch_shared(int layout, cudaStream_t st, const BatchArgs &A, const int32_t *act,
+                          int32_t n_act, int32_t j0, unsigned long long *ctr, int dev) {
+  static int per_sm[3][64] = {};
+  auto grid = [&](const void *f, int l) {
+    int b = (dev >= 0 && dev < 64) ? per_sm[l][dev] : 0;
+    if (!b) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, 0) != cudaSuccess || b < 1)
+        b = 1;
+      if (dev >= 0 && dev < 64) per_sm[l][dev] = b;
+    }
+    return sm_count(dev) * b;
+  };
+  cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st);
+  if (layout == kWide)
+    kb_shared_walks<kWide><<<grid((const void *)kb_shared_walks<kWide>, kWide), 256, 0, st>>>(
+        A, act, n_act, j0, ctr);
+  else if (layout == kCsr)
+    kb_shared_walks<kCsr><<<grid((const void *)kb_shared_walks<kCsr>, kCsr), 256, 0, st>>>(
+        A, act, n_act, j0, ctr);
+  else
+    kb_shared_walks<kNarrow><<<grid((const void *)kb_shared_walks<kNarrow>, kNarrow), 256, 0,
+                               st>>>(A, act, n_act, j0, ctr);
+}
+
 static std::mutex g_stream_mu;
 static cudaStream_t g_cap_stream[64] = {};
 
@@ -426,11 +622,12 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     return fail(SRK_EINVAL, "step_counts is not supported by srk_multi_source");
   if (opt && (opt->flags & SRK_OPT_LITERAL_SHUFFLE))
     return fail(SRK_EINVAL, "the literal shuffle is not supported by srk_multi_source");
-  if (opt && (opt->flags & ~(SRK_OPT_NO_GRAPH | SRK_OPT_WARMUP_RULE)))
+  if (opt && (opt->flags & ~(SRK_OPT_NO_GRAPH | SRK_OPT_WARMUP_RULE | SRK_OPT_SHARED_WALKS)))
     return fail(SRK_EINVAL, "unknown opts.flags 0x%x", opt->flags);
   if (opt && (opt->target_begin != 0 || opt->target_end != 0))
     return fail(SRK_EINVAL, "target ranges are not supported by srk_multi_source");
   const bool use_graph = !(opt && (opt->flags & SRK_OPT_NO_GRAPH));
+  const bool shared = opt && (opt->flags & SRK_OPT_SHARED_WALKS);
   const size_t n = (size_t)g->n;
   // a1 for every source (host, FP64)
   std::vector<QueryTab> tabs((size_t)k);
@@ -476,10 +673,14 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     size_t need = 0;
     int32_t i1 = i0;
     std::vector<size_t> ws_off;
-    while (i1 < k) {
+    while (i1 < k && !(shared && i1 - i0 >= 32)) {
       Workspace w;
-      const size_t b = align256(plan(tabs[i1], &w, nullptr)) +
-                       (d_scores ? 0 : align256(8 * n)) + (d_counts ? 0 : align256(4 * n));
+      const QueryTab &t1 = tabs[(size_t)i1];
+      const size_t b = align256(plan(t1, &w, nullptr)) +
+                       (d_scores ? 0 : align256(8 * n)) + (d_counts ? 0 : align256(4 * n)) +
+                       (shared ? align256(4 * (size_t)std::max(t1.L, 1) * t1.N_tot) +
+                                     align256(8 * (size_t)t1.N_tot)
+                               : 0);
       if (i1 > i0 && need + b > budget) break;
       ws_off.push_back(need);
       need += b;
@@ -487,11 +688,19 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     }
     const int32_t kb = i1 - i0;
     int Lmax = 0;
-    for (int32_t b = i0; b < i1; ++b) Lmax = std::max(Lmax, tabs[(size_t)b].L);
+    int32_t Jmax = 0, j0 = INT32_MAX;
+    for (int32_t b = i0; b < i1; ++b) {
+      const QueryTab &t = tabs[(size_t)b];
+      Lmax = std::max(Lmax, t.L);
+      Jmax = std::max(Jmax, t.N_tot);
+      j0 = std::min(j0, t.L >= 1 ? t.P[1] : t.N_tot);  // below, every pair has length 0
+    }
+    // shared walks: the step masks, Lmax + 1 rows of Jmax words
+    const size_t m_bytes = shared ? 4 * (size_t)(Lmax + 1) * (size_t)Jmax : 0;
     const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
                         align256(sizeof(int64_t) * (kb + 1)) +
                         align256(sizeof(int32_t) * (kb + 1)) +
-                        align256(sizeof(unsigned long long) * (kb + 1));
+                        align256(sizeof(unsigned long long) * (kb + 2)) + align256(m_bytes);
     char *base = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&base, head + need, mp, st);
     if (e != cudaSuccess) { rc = cuda_fail(e, "batch workspace allocation"); break; }
@@ -501,6 +710,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     int32_t *d_act_src = (int32_t *)((char *)d_off + align256(sizeof(int64_t) * (kb + 1)));
     unsigned long long *d_ctr = (unsigned long long *)((char *)d_act_src +
                                                          align256(sizeof(int32_t) * (kb + 1)));
+    uint32_t *d_M = (uint32_t *)((char *)d_ctr + align256(sizeof(unsigned long long) * (kb + 2)));
     // d_ctr[0] = item counter, d_ctr[1 + i] = steps of source i; n_act_src in d_act_src[kb]
     char *ws_base = base + head;
     std::vector<BatchSrc> hsrc((size_t)kb);
@@ -517,6 +727,15 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       if (!d_scores) extra += align256(8 * n);
       S.counts = !meet_counts ? nullptr
                  : (d_counts ? meet_counts + (size_t)(i0 + b) * n : (uint32_t *)extra);
+      if (meet_counts && !d_counts) extra += align256(4 * n);
+      S.Hj = nullptr;
+      S.wj = nullptr;
+      if (shared) {
+        S.Hj = (int32_t *)extra;
+        extra += align256(4 * (size_t)std::max(t.L, 1) * t.N_tot);
+        S.wj = (unsigned long long *)extra;
+        extra += align256(8 * (size_t)t.N_tot);
+      }
       S.steps = d_ctr + 1 + b;
       S.s = t.s;
       S.L = t.L;
@@ -547,6 +766,8 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     A.pos_bits = g->pos_bits;
     A.key0 = (uint32_t)seed;
     A.key1 = (uint32_t)(seed >> 32);
+    A.M = d_M;
+    A.Jmax = Jmax;
     const int gw = (int)std::max<int64_t>(1, std::min<int64_t>((A.total_walks + 255) / 256,
                                                                 (int64_t)sms * 8));
     auto enqueue_source_side = [&](cudaStream_t s2) {
@@ -564,8 +785,13 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       kb_fy_scatter<<<gw, 256, 0, s2>>>(A);
       kb_fy_groups<<<gw, 256, 0, s2>>>(A);
       kb_pairs<<<gw, 256, 0, s2>>>(A);
-      kb_rows<<<1, 256, 0, s2>>>(A, d_act_src, d_act_src + kb);
-      kb_hit_table<<<gw, 256, 0, s2>>>(A);
+      if (shared) {
+        cudaMemsetAsync(d_M, 0, m_bytes, s2);
+        kb_hitj<<<gw, 256, 0, s2>>>(A);
+      } else {
+        kb_rows<<<1, 256, 0, s2>>>(A, d_act_src, d_act_src + kb);
+        kb_hit_table<<<gw, 256, 0, s2>>>(A);
+      }
       const int gp = (int)std::min<int64_t>(((int64_t)kb * (int64_t)n + 255) / 256,
                                             (int64_t)sms * 16);
       kb_prefill<<<gp, 256, 0, s2>>>(d_src, kb, (int32_t)n);
@@ -577,7 +803,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     }
     // autotune the persistent kernel's launch shape on the first batch
     int shape = g->batch_cfg;
-    if (shape < 0 || shape >= kNumShapes) {
+    if (!shared && (shape < 0 || shape >= kNumShapes)) {
       enqueue_source_side(st);
       cudaEvent_t t0 = nullptr, t1 = nullptr;
       e = cudaEventCreate(&t0);
@@ -611,8 +837,11 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     }
     auto enqueue_all = [&](cudaStream_t s2) {
       enqueue_source_side(s2);
-      launch_targets(g->layout, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
-                     d_ctr, INT64_MAX, Lmax);
+      if (shared)
+        launch_shared(g->layout, s2, A, g->act, g->n_act, j0, d_ctr, dev);
+      else
+        launch_targets(g->layout, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
+                       d_ctr, INT64_MAX, Lmax);
     };
     if (use_graph) {
       cudaGraph_t graph = nullptr;

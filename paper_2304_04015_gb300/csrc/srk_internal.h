@@ -55,7 +55,8 @@ namespace srk {
 struct QueryTab {
   int32_t s, n, L, N_tot;
   uint32_t key0, key1;
-  int32_t literal, pad_;  // 1: literal target shuffle (SRK_OPT_LITERAL_SHUFFLE)
+  int32_t literal;  // 1: literal target shuffle (SRK_OPT_LITERAL_SHUFFLE)
+  int32_t shared;   // 1: shared target walks (SRK_OPT_SHARED_WALKS)
   double z;
   int32_t P[SRK_MAX_LEN + 2];  // stratum prefix: walk r has length l iff P[l] <= r < P[l+1]
   double a[SRK_MAX_LEN + 1];   // rounding weight a(l) = |Z_l| / |Z^_l|
@@ -124,6 +125,10 @@ int target_range(const srk_graph *g, const srk_opts *opt, int32_t *b, int32_t *e
 // Exclusive scan of cnt[0..N) into off[0..N] (one block of 1024 threads).
 __global__ void k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off,
                        int32_t N);
+
+// Philox counter word 3 of the target walks: the source, or this constant
+// with SRK_OPT_SHARED_WALKS (sources are below 2^31, so it names none).
+constexpr uint32_t kSharedWalkKey = 0xFFFFFFFEu;
 
 // Releases the graph's linear topology, if built (srk_linear.cu).
 void free_lin_topo(srk_graph *g);

@@ -101,7 +101,8 @@ extern "C" int srk_single_source_noalloc(const srk_graph *g, int32_t s, double c
   clear_error();
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (!scores) return fail(SRK_EINVAL, "scores is null");
-  if (opt && (opt->flags & ~(SRK_OPT_WARMUP_RULE | SRK_OPT_LITERAL_SHUFFLE)))
+  if (opt && (opt->flags & ~(SRK_OPT_WARMUP_RULE | SRK_OPT_LITERAL_SHUFFLE |
+                             SRK_OPT_SHARED_WALKS)))
     return fail(SRK_EINVAL, "unsupported opts.flags 0x%x", opt->flags);
   uint32_t *step_counts = opt ? opt->step_counts : nullptr;
   QueryTab t;

@@ -277,6 +277,7 @@ struct TargetArgs {
   const int32_t *npos;     // 4-byte-entry layout: node positions
   int32_t pos_bits;
   int32_t n, s, L;
+  uint32_t walk_key;       // Philox counter word 3 of the target walks (s or shared)
   uint32_t key0, key1;
   double z;
   const int32_t *small_base;
@@ -329,7 +330,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   S.pair_w = A.pair_w;
   S.Hc = A.Hc;
   S.n_pairs = cnt[1];
-  S.s = (uint32_t)A.s;
+  S.s = A.walk_key;
   FeistelShape fs;
   if constexpr (kLiteral)
     fs = feistel_shape(A.N_tot, ((uint64_t)A.key1 << 32) | A.key0, (uint32_t)A.s);
@@ -476,6 +477,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.pos_bits = g->pos_bits;
   A.n = g->n;
   A.s = t.s;
+  A.walk_key = t.shared ? kSharedWalkKey : (uint32_t)t.s;
   A.L = t.L;
   A.key0 = t.key0;
   A.key1 = t.key1;
@@ -568,7 +570,8 @@ extern "C" int srk_single_source(const srk_graph *g, int32_t s, double c,
   clear_error();
   if (!g) return fail(SRK_EINVAL, "null graph");
   if (!scores) return fail(SRK_EINVAL, "scores is null");
-  if (opt && (opt->flags & ~(SRK_OPT_WARMUP_RULE | SRK_OPT_LITERAL_SHUFFLE)))
+  if (opt && (opt->flags & ~(SRK_OPT_WARMUP_RULE | SRK_OPT_LITERAL_SHUFFLE |
+                             SRK_OPT_SHARED_WALKS)))
     return fail(SRK_EINVAL, "unsupported opts.flags 0x%x", opt->flags);
   QueryTab t;
   int rc = build_table(g->n, s, c, eps, seed, opt, &t);
