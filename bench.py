@@ -87,6 +87,9 @@ def parse():
                     help="serve: latency target of the admission (0: memory only, FIFO)")
     ap.add_argument("--batch-sources", type=int, default=12,
                     help="sources of the 4096-source batching list that are run")
+    ap.add_argument("--topk", type=int, default=0,
+                    help="batch: return each source's top-k targets (srk_multi_source_topk) "
+                         "instead of dense rows; the plain comparison is skipped")
     ap.add_argument("--shared-walks", action="store_true",
                     help="batch: target walks drawn once for all sources of a batch "
                          "(SRK_OPT_SHARED_WALKS), against one query per launch with the "
@@ -339,6 +342,8 @@ def run_batch(args, rank, world):
     eps = [float(all_eps[i]) for i in pick]
     g = srk.srk_graph_load(rp_d, col_d, layout=args.layout)
     k = len(sources)
+    if args.topk > 0:
+        return run_batch_topk(args, srk, torch, dev, g, rp, n, m, sources, eps, pick, t_gen)
     out = torch.empty((k, n), dtype=torch.float64, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     sw = args.shared_walks
@@ -395,6 +400,52 @@ def run_batch(args, rank, world):
             "adjacency": srk.srk_graph_layout(g),
             "roofline": roofline, "gather_roofline": gather, "cpu_baseline": base,
             "note": "subset of the 4096-source list; the full list is ~1e15 walk steps"}
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
+def run_batch_topk(args, srk, torch, dev, g, rp, n, m, sources, eps, pick, t_gen):
+    """The batching list through the sparse output: every source's top-k
+    targets (srk_multi_source_topk), timed with CUDA events over the whole
+    call; no dense k x n matrix exists at any time."""
+    k, top = len(sources), args.topk
+    tn = torch.empty((k, top), dtype=torch.int32, device=dev)
+    ts = torch.empty((k, top), dtype=torch.float64, device=dev)
+    tc = torch.empty(k, dtype=torch.int32, device=dev)
+    nz = torch.empty(k, dtype=torch.int64, device=dev)
+    sw = args.shared_walks
+    srk.srk_multi_source_topk(g, sources[:3], C, eps[:3], QUERY_SEED, top, tn[:3], ts[:3],
+                              shared_walks=sw)   # warm-up (autotuner)
+    torch.cuda.synchronize()
+    st = srk.SrkStats()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    srk.srk_multi_source_topk(g, sources, C, eps, QUERY_SEED, top, tn, ts, tc, nz, stats=st,
+                              shared_walks=sw)
+    ev[1].record()
+    ev[1].synchronize()
+    t = ev[0].elapsed_time(ev[1]) / 1e3
+    deg = np.diff(rp)
+    groups = {"top in-degree": 0, "median in-degree": 0, "no in-neighbours": 0}
+    third = 4096 // 3
+    for i in pick:
+        groups[("top in-degree", "median in-degree", "no in-neighbours")[min(2, i // third)]] += 1
+    nzh = nz.cpu().numpy()
+    line = {"metric": "batched multi-source queries/s with top-%d output (R-MAT scale %d, "
+                      "mixed eps)" % (top, args.batch_scale),
+            "workload": "batch_rmat%d_mixed_sources_mixed_eps_top%d%s"
+                        % (args.batch_scale, top, "_shared_walks" if sw else ""),
+            "value": k / t, "unit": "queries/s", "higher_is_better": True, "seconds": t,
+            "sources": k, "source_groups": groups, "eps_counts": {str(e): eps.count(e) for e in
+                                                                  sorted(set(eps))},
+            "n": n, "m": m, "top": top, "target_steps": st.target_steps,
+            "walk_steps_per_s": st.target_steps / t,
+            "nnz_per_source": {"min": int(nzh.min()), "median": float(np.median(nzh)),
+                               "max": int(nzh.max())},
+            "output_bytes": k * top * 12, "dense_bytes_avoided": k * n * 8,
+            "adjacency": srk.srk_graph_layout(g), "graph_gen_s": t_gen,
+            "source_in_degrees": [int(deg[s]) for s in sources]}
     print(json.dumps(line), flush=True)
     g.close()
     return 0

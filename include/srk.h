@@ -109,7 +109,12 @@ typedef struct srk_stats {
     int32_t batch_shape;    /* srk_multi_source: index of the persistent kernel's
                                launch shape the autotuner chose; else -1 */
     uint64_t source_steps;  /* steps taken by the source's walks */
-    uint64_t target_steps;  /* target-walk steps taken over all targets */
+    uint64_t target_steps;  /* target-walk steps taken over all targets (with
+                               SRK_OPT_SHARED_WALKS in srk_multi_source: the
+                               steps of the shared walks) */
+    int64_t graph_updates;  /* srk_multi_source: batches launched by updating
+                               the graph handle's cached CUDA-graph executable
+                               instead of instantiating one (this call) */
 } srk_stats;
 
 /* Query options; pass NULL for the paper's defaults. */
@@ -234,6 +239,31 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
                      double c, const double *eps, uint64_t seed,
                      const srk_opts *opt, double *scores,
                      uint32_t *meet_counts, void *cuda_stream);
+
+/*
+ * srk_multi_source_topk -- srk_multi_source with a sparse output: for each
+ * source, its `top` most similar targets.  Section 5.5 ends with every
+ * machine holding the scores s~(s, u) of its targets; for many sources the
+ * dense k x n matrix is too large to keep (4,096 sources of a 16.8M-node
+ * graph: 550 GB), so this call keeps per source only
+ *   top_nodes  : k x top int32 (device): row i lists the targets u != s_i of
+ *                largest s~(s_i, u), score descending, ties by smaller id;
+ *                -1 after the last nonzero score;
+ *   top_scores : k x top FP64 (device): their scores (0 after the last);
+ *   top_count  : NULL or k int32 (device): entries filled, min(top, nnz);
+ *   nnz        : NULL or k int64 (device): targets with a nonzero score.
+ * The scores are exactly those of srk_multi_source (same options, including
+ * SRK_OPT_SHARED_WALKS).  Sources run in chunks whose dense rows fit a
+ * scratch budget (an eighth of free device memory, at most 4 GiB, or the
+ * byte count in SRK_TOPK_ROWS_BYTES); each chunk's rows are selected on the
+ * device by a radix select over the scores' bit patterns.  1 <= top <= 4096
+ * (SRK_EINVAL otherwise); host output pointers are refused (SRK_EINVAL).
+ */
+int srk_multi_source_topk(const srk_graph *g, const int32_t *sources, int32_t k,
+                          double c, const double *eps, uint64_t seed,
+                          const srk_opts *opt, int32_t top, int32_t *top_nodes,
+                          double *top_scores, int32_t *top_count, int64_t *nnz,
+                          void *cuda_stream);
 
 /*
  * srk_linear_fwd -- truncated linearised single-source SimRank (Appendix A:

@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "SrkError", "SrkOpts", "SrkStats", "Graph",
     "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout", "srk_single_source",
-    "srk_multi_source", "srk_single_source_noalloc", "srk_probe_gather",
+    "srk_multi_source", "srk_multi_source_topk", "srk_single_source_noalloc", "srk_probe_gather",
     "srk_probe_gather_ex", "SRK_PROBE_DEFAULT", "SRK_PROBE_CG", "SRK_PROBE_NC", "SRK_PROBE_CA",
     "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free", "LinearContext",
     "LinearSimRank", "linear_simrank", "SrkServerReport", "Server",
@@ -61,7 +61,7 @@ class SrkStats(ctypes.Structure):
     _fields_ = [("z", ctypes.c_double), ("L", ctypes.c_int32),
                 ("n_walks", ctypes.c_int32), ("n_active_pairs", ctypes.c_int32),
                 ("batch_shape", ctypes.c_int32), ("source_steps", ctypes.c_uint64),
-                ("target_steps", ctypes.c_uint64)]
+                ("target_steps", ctypes.c_uint64), ("graph_updates", ctypes.c_int64)]
 
 
 class SrkOpts(ctypes.Structure):
@@ -118,7 +118,10 @@ _lib.srk_pool_stats.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
 _lib.srk_last_error.restype = ctypes.c_char_p
-for _f in ("srk_pool_stats", "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout",
+_lib.srk_multi_source_topk.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_double, _vp,
+                                       ctypes.c_uint64, _vp, ctypes.c_int32, _vp, _vp, _vp,
+                                       _vp, _vp]
+for _f in ("srk_pool_stats", "srk_multi_source_topk", "srk_graph_load", "srk_graph_free", "srk_graph_info", "srk_graph_layout",
            "srk_single_source", "srk_single_source_noalloc", "srk_multi_source",
            "srk_probe_gather", "srk_probe_gather_ex", "srk_linear_fwd", "srk_linear_bwd", "srk_linear_ctx_free",
            "srk_server_create", "srk_server_submit", "srk_server_drain", "srk_server_stats",
@@ -349,6 +352,33 @@ def srk_multi_source(g: Graph, sources, c: float, eps, seed: int, scores,
                                int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), sc, mc,
                                _stream_handle(stream))
     del k1, k2
+    _check(rc)
+
+
+def srk_multi_source_topk(g: Graph, sources, c: float, eps, seed: int, top: int,
+                          top_nodes, top_scores, top_count=None, nnz=None, *,
+                          z_override=None, L_override=None, p=None, q=None,
+                          stats: Optional[SrkStats] = None, no_graph: bool = False,
+                          warmup_rule: bool = False, shared_walks: bool = False,
+                          stream=None) -> None:
+    """Per source, the ``top`` targets of largest score (``srk_multi_source_topk``):
+    ``top_nodes`` (k x top int32), ``top_scores`` (k x top float64) and
+    optionally ``top_count`` (k int32) and ``nnz`` (k int64), all device
+    tensors."""
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    k = src.size
+    eps_a = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (k,)))
+    tn, _, k1 = _ptr(top_nodes, "int32")
+    ts, _, k2 = _ptr(top_scores, "float64")
+    tc, _, k3 = _ptr(top_count, "int32")
+    nz, _, k4 = _ptr(nnz, "int64")
+    o, k5 = _opts(z_override, L_override, p, q, None, stats,
+                  flags=SRK_OPT_NO_GRAPH if no_graph else 0, warmup_rule=warmup_rule,
+                  shared_walks=shared_walks)
+    rc = _lib.srk_multi_source_topk(g.handle, src.ctypes.data, k, float(c), eps_a.ctypes.data,
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), int(top),
+                                    tn, ts, tc, nz, _stream_handle(stream))
+    del k1, k2, k3, k4, k5
     _check(rc)
 
 

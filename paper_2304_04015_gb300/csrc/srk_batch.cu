@@ -591,6 +591,11 @@ static void launch_shared(int layout, cudaStream_t st, const BatchArgs &A, const
 static std::mutex g_stream_mu;
 static cudaStream_t g_cap_stream[64] = {};
 
+// One lock per device around a batch's capture and graph launch: the capture
+// stream and the handles' cached executables are shared.
+static std::mutex g_capture_mu[64];
+static std::mutex &capture_mutex(int dev) { return g_capture_mu[dev >= 0 && dev < 64 ? dev : 0]; }
+
 // A library-owned non-blocking stream per device for graph capture (the
 // caller's stream may be the legacy default stream, which cannot capture).
 static cudaStream_t capture_stream(int dev) {
@@ -844,21 +849,35 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
                        d_ctr, INT64_MAX, Lmax);
     };
     if (use_graph) {
+      // The batch is captured every time (its buffers move), but the graph's
+      // executable is kept in the handle and only updated with the new
+      // parameters while the launch sequence keeps its shape (same kernels,
+      // same order); otherwise it is instantiated anew.
+      std::lock_guard<std::mutex> lk(capture_mutex(dev));
+      srk_graph *gm = const_cast<srk_graph *>(g);
       cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      cudaEventRecord(ev_in, st);
-      cudaStreamWaitEvent(cs, ev_in, 0);
-      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      e = cudaEventRecord(ev_in, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in, 0);
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
         enqueue_all(cs);
         e = cudaStreamEndCapture(cs, &graph);
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-      if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+      if (e == cudaSuccess && gm->batch_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(gm->batch_exec, graph, &info) != cudaSuccess) {
+          cudaGetLastError();  // a different shape: instantiate below
+          cudaGraphExecDestroy(gm->batch_exec);
+          gm->batch_exec = nullptr;
+        } else {
+          ++total.graph_updates;
+        }
+      }
+      if (e == cudaSuccess && !gm->batch_exec) e = cudaGraphInstantiate(&gm->batch_exec, graph, 0);
+      if (e == cudaSuccess) e = cudaGraphLaunch(gm->batch_exec, cs);
       if (e == cudaSuccess) e = cudaEventRecord(ev_out, cs);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_out, 0);
       if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-      if (exec) cudaGraphExecDestroy(exec);
       if (graph) cudaGraphDestroy(graph);
     } else {
       enqueue_all(st);

@@ -354,6 +354,7 @@ extern "C" int srk_graph_free(srk_graph *g) {
     if (g->adj) cudaFree(g->adj);
     if (g->npos) cudaFree(g->npos);
     if (g->act) cudaFree(g->act);
+    if (g->batch_exec) cudaGraphExecDestroy(g->batch_exec);
     free_lin_topo(g);
   }
   delete g;

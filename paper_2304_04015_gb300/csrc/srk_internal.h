@@ -40,6 +40,9 @@ struct srk_graph {
   // Launch shape of the batched target kernel chosen by the autotuner
   // (-1: not tuned yet).
   int batch_cfg = -1;
+  // Executable of the last captured batch (srk_multi_source with a CUDA
+  // graph), updated in place for the next batch of the same shape.
+  cudaGraphExec_t batch_exec = nullptr;
   // Topology of the linearised form (edge owners, a transpose, list size
   // classes), built by the first srk_linear_fwd on the graph.
   struct srk_lin_topo *lin = nullptr;

@@ -680,3 +680,32 @@ def test_multi_source_options_equal_single_queries(srk, opts):
         assert int(mc.sum()) > 0
     finally:
         g.close()
+
+
+def test_batched_graph_executable_is_updated_not_rebuilt(srk):
+    # the second call of the same shape launches the cached executable after
+    # updating its parameters; a call of another shape rebuilds it; results
+    # stay equal to single queries throughout
+    import torch
+    dev = torch.device("cuda:0")
+    rp, col = rmat_graph(14)
+    n = rp.size - 1
+    deg = np.diff(rp)
+    order = np.argsort(-deg, kind="stable")
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
+    try:
+        single = torch.empty(n, dtype=torch.float64, device=dev)
+        for sources, expect_update in (([int(order[0]), int(order[50])], False),
+                                       ([int(order[1]), int(order[60])], True),
+                                       ([int(order[2])], False),
+                                       ([int(order[3])], True)):
+            out = torch.empty((len(sources), n), dtype=torch.float64, device=dev)
+            st = srk.SrkStats()
+            srk.srk_multi_source(g, sources, C, 0.1, 3, out, stats=st)
+            torch.cuda.synchronize()
+            assert (st.graph_updates >= 1) == expect_update
+            for i, s in enumerate(sources):
+                srk.srk_single_source(g, s, C, 0.1, 3, single)
+                assert torch.equal(single, out[i])
+    finally:
+        g.close()
