@@ -377,10 +377,12 @@ def run_batch(args, rank, world):
                 "peak_kind": peak_kind + " (HBM copy)", "bytes_per_unit": BYTES_PER_STEP,
                 "unit_name": "target-walk step",
                 "note": "whole batch time (the source phases are a few percent)"}
-    probe = gather_probe(srk, torch, dev, n + m)[0]
-    gather = {"probe_gathers_per_s_graph_sized": probe,
-              "kernel_steps_per_s": st.target_steps / t_batch,
-              "frac_of_graph_sized_probe": st.target_steps / t_batch / probe}
+    gather = None
+    if not args.skip_probe:
+        probe = gather_probe(srk, torch, dev, n + m)[0]
+        gather = {"probe_gathers_per_s_graph_sized": probe,
+                  "kernel_steps_per_s": st.target_steps / t_batch,
+                  "frac_of_graph_sized_probe": st.target_steps / t_batch / probe}
     base = None
     if not args.no_cpu_baseline:
         col_h = col_d.cpu().numpy()
