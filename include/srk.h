@@ -389,11 +389,13 @@ int srk_pool_stats(int32_t device, uint64_t *reserved, uint64_t *used, uint64_t 
  *   n_workers: worker threads / streams (1..64); latency_target_ms: 0 for
  *   memory-only admission and first-in-first-out service, else a target for
  *   the estimated time to finish all admitted work including the new request,
- *   with shortest-estimated-work-first service.  The estimate is (nodes with
- *   in-neighbours) x N_tot x 0.8 walk steps per request (0 when the source
- *   has no in-neighbours), divided by the rate at which completed requests
- *   got through their estimate (exponential average, starting at 5e10/s).
- *   Copies each graph's row_ptr to the host once.
+ *   with shortest-estimated-work-first service.  The estimate of a request
+ *   is (nodes with in-neighbours) x N_tot x (walk steps per pair) / (walk
+ *   steps per second), 0 when the source has no in-neighbours; both figures
+ *   are kept per graph, measured at creation by four queries with z = 256
+ *   from evenly spaced nodes with in-neighbours, and refined by every
+ *   completed request (exponential averages).  Copies each graph's row_ptr
+ *   to the host once.
  * srk_server_submit -- enqueue one srk_single_source query on graph index
  *   `graph`.  The request is admitted if the memory it needs fits in what the
  *   budget leaves (and, with a latency target, its estimated finish fits the

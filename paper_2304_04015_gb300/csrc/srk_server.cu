@@ -11,13 +11,16 @@
 // records the latency from submission to the result being on the host.
 //
 // With a latency target, admission also needs the request's estimated finish
-// time to fit it: the server estimates a request's work as (targets with
-// in-neighbours) x N_tot x kStepsPerPair walk steps (none when the source has
-// no in-neighbours: its walks cannot leave it), keeps the estimated work of
-// admitted, unfinished requests, and divides by the rate at which completed
-// requests got through their estimated work (an exponential average).  The
-// queue is then served shortest estimated work first, so short queries are
-// not held behind long ones; without a target it is first in, first out.
+// time to fit it.  Per graph the server keeps two figures, measured when it is
+// created by a few small calibration queries and refined by every completed
+// request (exponential averages): the walk steps per (target, pair) and the
+// walk steps per second of service.  A request's estimated time is (targets
+// with in-neighbours) x N_tot x steps per pair / steps per second (none when
+// the source has no in-neighbours: its walks cannot leave it); a request is
+// admitted when the estimated time of the admitted, unfinished requests plus
+// its own fits the target.  The queue is then served shortest estimated time
+// first, so short queries are not held behind long ones; without a target it
+// is first in, first out.
 #include <stdint.h>
 #include <string.h>
 
@@ -41,25 +44,27 @@ struct Request {
   uint64_t seed, tag;
   double *host_scores;
   size_t bytes;  // reserved device memory
-  double work;   // estimated walk steps
+  double pairs;  // (targets with in-neighbours) x N_tot, 0 when s has none
+  double work;   // estimated seconds of service
   uint64_t order;
   Clock::time_point t_submit;
 };
 
-// walk steps per (target, pair) the work estimate assumes before any request
-// has completed; completed requests refine the rate, not this factor
-constexpr double kStepsPerPair = 0.8;
+// Calibration of a graph at server creation: this many queries from evenly
+// spaced nodes with in-neighbours, each with z = kCalibZ walks per pair.
+constexpr int kCalibQueries = 4;
+constexpr double kCalibZ = 256.0;
 
 }  // namespace
 
 struct srk_server {
   std::vector<const srk_graph *> graphs;
   std::vector<std::vector<uint8_t>> has_in;  // per graph: node has in-neighbours
+  std::vector<double> steps_per_pair;        // per graph: walk steps per (target, pair)
+  std::vector<double> steps_per_s;           // per graph: walk steps per second of service
   size_t budget = 0;
   double target_ms = 0.0;     // 0: memory-only admission, FIFO
-  double rate = 5.0e10;       // estimated work units (walk steps) per second,
-                              // refined on completions; starts conservative
-  double queued_work = 0.0;   // estimated steps of admitted, unfinished requests
+  double queued_work = 0.0;   // estimated seconds of admitted, unfinished requests
   uint64_t next_order = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_idle;
@@ -126,8 +131,13 @@ static void worker_main(srk_server *srv, int device) {
         ++srv->completed;
         srv->target_steps += stats.target_steps;
         const double secs = std::chrono::duration<double>(t_done - t_start).count();
-        if (r.work > 1.0e6 && secs > 0.0)  // estimated work per second of service
-          srv->rate = 0.8 * srv->rate + 0.2 * (r.work / secs);
+        const double steps = (double)stats.target_steps;
+        if (r.pairs > 0.0 && steps > 1.0e6 && secs > 0.0) {  // refine the graph's figures
+          double &spp = srv->steps_per_pair[(size_t)r.graph];
+          double &sps = srv->steps_per_s[(size_t)r.graph];
+          spp = 0.8 * spp + 0.2 * (steps / r.pairs);
+          sps = 0.8 * sps + 0.2 * (steps / secs);
+        }
         srv->latency_ms.push_back(
             std::chrono::duration<double, std::milli>(t_done - r.t_submit).count());
         srv->t_last = t_done;
@@ -184,6 +194,59 @@ extern "C" int srk_server_create(const srk_graph *const *graphs, int32_t n_graph
     for (size_t v = 0; v < has.size(); ++v) has[v] = rp[v + 1] > rp[v];
     srv->has_in.push_back(std::move(has));
   }
+  // calibration: steps per pair and steps per second of each graph
+  for (int32_t i = 0; i < n_graphs; ++i) {
+    const srk_graph *g = graphs[i];
+    const std::vector<uint8_t> &has = srv->has_in[(size_t)i];
+    std::vector<int32_t> act;
+    for (size_t v = 0; v < has.size(); ++v)
+      if (has[v]) act.push_back((int32_t)v);
+    double spp = 0.8, sps = 5.0e10;  // used when the graph has no walk steps
+    if (!act.empty()) {
+      DeviceGuard guard(g->device);
+      double *d = nullptr;
+      cudaStream_t st = nullptr;
+      cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaMallocFromPoolAsync((void **)&d, sizeof(double) * (size_t)g->n, pool(g->device),
+                                    st);
+      double steps = 0.0, pairs = 0.0, secs = 0.0;
+      for (int k = 0; k < kCalibQueries && e == cudaSuccess; ++k) {
+        const int32_t s = act[act.size() * (size_t)(2 * k + 1) / (2 * kCalibQueries)];
+        srk_stats stats;
+        srk_opts opt;
+        memset(&opt, 0, sizeof opt);
+        opt.L_override = -1;
+        opt.z_override = kCalibZ;
+        opt.stats = &stats;
+        const Clock::time_point t0 = Clock::now();
+        if (srk_single_source(g, s, 0.6, 0.5, 1, &opt, d, nullptr, nullptr, st) != SRK_OK ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+          e = cudaErrorUnknown;
+          break;
+        }
+        secs += std::chrono::duration<double>(Clock::now() - t0).count();
+        steps += (double)stats.target_steps;
+        pairs += (double)g->n_act * (double)stats.n_walks;
+      }
+      if (d) cudaFreeAsync(d, st);
+      if (st) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+      }
+      if (e != cudaSuccess) {
+        delete srv;
+        return fail(SRK_ECUDA, "srk_server_create: calibrating graph %d: %s", i,
+                    srk_last_error());
+      }
+      if (steps > 0.0 && pairs > 0.0 && secs > 0.0) {
+        spp = steps / pairs;
+        sps = steps / secs;
+      }
+    }
+    srv->steps_per_pair.push_back(spp);
+    srv->steps_per_s.push_back(sps);
+  }
   const int device = graphs[0]->device;
   for (int32_t w = 0; w < n_workers; ++w) srv->workers.emplace_back(worker_main, srv, device);
   *out = srv;
@@ -204,9 +267,8 @@ extern "C" int srk_server_submit(srk_server *srv, int32_t graph, int32_t s, doub
   if (rc) return rc;
   Workspace w;
   const size_t bytes = plan(t, &w, nullptr) + sizeof(double) * (size_t)g->n;
-  const double work = srv->has_in[(size_t)graph][(size_t)s]
-                          ? (double)g->n_act * (double)t.N_tot * kStepsPerPair
-                          : 0.0;
+  const double pairs =
+      srv->has_in[(size_t)graph][(size_t)s] ? (double)g->n_act * (double)t.N_tot : 0.0;
   Request r;
   r.graph = graph;
   r.s = s;
@@ -216,17 +278,18 @@ extern "C" int srk_server_submit(srk_server *srv, int32_t graph, int32_t s, doub
   r.tag = tag;
   r.host_scores = host_scores;
   r.bytes = bytes;
-  r.work = work;
+  r.pairs = pairs;
   r.t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(srv->mu);
+  const double work = pairs * srv->steps_per_pair[(size_t)graph] / srv->steps_per_s[(size_t)graph];
+  r.work = work;
   ++srv->submitted;
   if (!srv->have_first) {
     srv->have_first = true;
     srv->t_first = r.t_submit;
   }
   const bool mem_ok = srv->reserved + bytes <= srv->budget;
-  const bool time_ok = srv->target_ms <= 0.0 ||
-                       (srv->queued_work + work) / srv->rate * 1e3 <= srv->target_ms;
+  const bool time_ok = srv->target_ms <= 0.0 || (srv->queued_work + work) * 1e3 <= srv->target_ms;
   if (!mem_ok || !time_ok) {
     ++srv->shed;
     return SRK_OK;
