@@ -17,8 +17,9 @@ struct srk_graph {
   // in-degree d < deg_max = 2^(32-pos_bits) - 1 has the word d at its
   // position and its list right after it; a hub (d >= deg_max) has two words
   // {d, offset of its list} at position 2r of the hub region at the front,
-  // r its rank by how often walks land on it (so the hot headers share
-  // sectors), and its list after the other nodes'.  Entry k of v's list holds
+  // r its rank by how often walks visit it (so the hot headers share
+  // sectors), and its list after the other nodes'.  The other nodes' words
+  // follow in the order of expected visits per list entry (build_narrow).  Entry k of v's list holds
   // the k-th in-neighbour y as (min(|I(y)|, deg_max) << pos_bits) | npos[y],
   // so a walk step learns the next node's degree from the entry it reads and
   // reads a header only at a hub.
