@@ -87,6 +87,8 @@ def parse():
                     help="serve: latency target of the admission (0: memory only, FIFO)")
     ap.add_argument("--batch-sources", type=int, default=12,
                     help="sources of the 4096-source batching list that are run")
+    ap.add_argument("--batch-eps", type=float, default=0.0,
+                    help="batch: one eps for every source instead of the list's mixed eps")
     ap.add_argument("--topk", type=int, default=0,
                     help="batch: return each source's top-k targets (srk_multi_source_topk) "
                          "instead of dense rows; the plain comparison is skipped")
@@ -340,6 +342,8 @@ def run_batch(args, rank, world):
     pick = order[:args.batch_sources]
     sources = [int(all_src[i]) for i in pick]
     eps = [float(all_eps[i]) for i in pick]
+    if args.batch_eps > 0:
+        eps = [args.batch_eps] * len(sources)
     g = srk.srk_graph_load(rp_d, col_d, layout=args.layout)
     k = len(sources)
     if args.topk > 0:
@@ -390,8 +394,9 @@ def run_batch(args, rank, world):
         base = cpu_baseline_mix([(rp, col_h)], mix, args.cpu_seconds)
         del col_h
     line = {"metric": "batched multi-source queries/s (R-MAT scale %d, mixed eps)" % args.batch_scale,
-            "workload": "batch_rmat%d_mixed_sources_mixed_eps%s" % (args.batch_scale,
-                                                                   "_shared_walks" if sw else ""),
+            "workload": "batch_rmat%d_mixed_sources_%s%s" % (
+                args.batch_scale, "eps%g" % args.batch_eps if args.batch_eps > 0 else "mixed_eps",
+                "_shared_walks" if sw else ""),
             "shared_walks": sw, "plain_target_steps": plain_steps,
             "value": k / t_batch, "unit": "queries/s", "higher_is_better": True,
             "plain_value": k / t_plain, "batched_over_plain": t_plain / t_batch,

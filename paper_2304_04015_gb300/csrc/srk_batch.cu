@@ -34,8 +34,6 @@ struct BatchSrc {
   double *scores;         // output row, n entries
   uint32_t *counts;       // output row or null
   unsigned long long *steps;  // target-walk steps of this source (one counter)
-  int32_t *Hj;                // shared walks: node of source walk sigma(j) at step i,
-                              // at Hj[(i-1) N_tot + j] for i <= cap(j)
   unsigned long long *wj;     // shared walks: quantised Lemma 7 weight of pair j
   int32_t s, L, N_tot;
   double z;
@@ -54,6 +52,8 @@ struct BatchArgs {
   uint32_t key0, key1;
   uint32_t *M;    // shared walks: bit b of M[(i-1) Jmax + j] = pair j of batch
                   // source b may still meet at step i (cap_b(j) >= i); Lmax + 1 rows
+  int32_t *H;     // shared walks: H[((i-1) Jmax + j) k + b] = node of source b's walk
+                  // sigma_b(j) at step i, for i <= cap_b(j): one record per (step, pair)
   int32_t Jmax;   // shared walks: the largest N_tot of the batch
 };
 
@@ -325,8 +325,11 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
 // batch: it goes on while some source's pair j can still meet (it has not met
 // and its cap is not reached) and stops at a node without in-neighbours.  For
 // source b the pair meets at the first step i <= cap_b(j) where the walk is
-// at Hj_b[(i-1) N_b + j], exactly as srk_single_source with the same flag
-// decides it.  Batches hold at most 32 sources (one mask bit each).
+// at the node of source b's walk sigma_b(j) at step i, exactly as
+// srk_single_source with the same flag decides it.  Those nodes of all the
+// batch's sources sit together in one record per (step, pair), so the test of
+// every pending source reads one line.  Batches hold at most 32 sources (one
+// mask bit each).
 
 // Per source and pair j: the pair's weight, its hit-table column (steps
 // 1..cap(j) of source walk sigma(j)) and its bit in the step masks.
@@ -342,7 +345,7 @@ __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
     const int32_t *sp = S_.w.spos + (int64_t)w * Ls;
     const uint32_t bit = 1u << i_;
     for (int q = 1; q <= cap; ++q) {
-      S_.Hj[(int64_t)(q - 1) * S_.N_tot + j] = sp[q - 1];
+      A.H[((int64_t)(q - 1) * A.Jmax + j) * A.k + i_] = sp[q - 1];
       atomicOr(&A.M[(int64_t)(q - 1) * A.Jmax + j], bit);
     }
   })
@@ -350,7 +353,6 @@ __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
 
 // The batch's sources as the shared-walk kernel reads them (shared memory).
 struct ShSrc {
-  const int32_t *Hj;
   const unsigned long long *wj;
   double *scores;
   uint32_t *counts;
@@ -358,31 +360,61 @@ struct ShSrc {
   int32_t N, s;
 };
 
-// Meetings at step i of walk j (node x) for the sources in `pend`: each
-// source whose hit-table entry equals x counts the pair once (count and
-// weight into the warp's accumulators) and leaves `pend`.
-__device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, uint32_t pend, int i, int32_t j,
-                                                int32_t x, uint32_t *cnt,
-                                                unsigned long long *wsum) {
-  for (uint32_t m = pend; m; m &= m - 1) {
-    const int b = __ffs(m) - 1;
-    const ShSrc &S = src[b];
-    if (S.Hj[(int64_t)(i - 1) * S.N + j] == x) {
-      atomicAdd(&cnt[b], 1u);
-      atomicAdd(&wsum[b], S.wj[j]);
-      pend &= ~(1u << b);
+// The meeting test after a step, in one of two forms.  kCoop = false: each
+// stepping lane checks its own pending sources, reading their entries of its
+// record, and counts meetings with shared-memory atomics (cnt, wsum, indexed
+// by source).  kCoop = true, for batches whose pairs are pending for many
+// sources at once: the whole warp checks together -- for every stepping lane
+// l (node x_l, pair j_l, record offset r_l, pending sources p_l) lane b
+// compares the node of source b's walk, H[r_l + b], with x_l, so one
+// coalesced line serves all of lane l's sources, and lane b counts source
+// b's meetings in registers (c_b, w_b).  Returns the sources that met on this
+// lane's own pair.
+template <bool kCoop>
+__device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t *H, int k,
+                                                bool stepped, int32_t x, uint32_t rec,
+                                                uint32_t pend, int32_t j, int lane,
+                                                uint32_t *cnt, unsigned long long *wsum,
+                                                uint32_t &c_b, unsigned long long &w_b) {
+  uint32_t mine = 0u;
+  if constexpr (!kCoop) {
+    if (stepped)
+      for (uint32_t m = pend; m; m &= m - 1) {
+        const int b = __ffs(m) - 1;
+        if (H[rec + (uint32_t)b] == x) {
+          atomicAdd(&cnt[b], 1u);
+          atomicAdd(&wsum[b], src[b].wj[j]);
+          mine |= 1u << b;
+        }
+      }
+  } else {
+    for (uint32_t m = __ballot_sync(0xffffffffu, stepped && pend != 0u); m; m &= m - 1) {
+      const int l = __ffs(m) - 1;
+      const int32_t xl = __shfl_sync(0xffffffffu, x, l);
+      const uint32_t rl = __shfl_sync(0xffffffffu, rec, l);
+      const uint32_t pl = __shfl_sync(0xffffffffu, pend, l);
+      const int32_t jl = __shfl_sync(0xffffffffu, j, l);
+      const bool hit = lane < k && ((pl >> lane) & 1u) && H[rl + (uint32_t)lane] == xl;
+      const uint32_t met = __ballot_sync(0xffffffffu, hit);
+      if (lane == l) mine = met;
+      if (hit) {
+        ++c_b;
+        w_b += src[lane].wj[jl];
+      }
     }
   }
-  return pend;
+  return mine;
 }
 
 // a4+a5 of a batch with shared target walks: warps take targets (the nodes
 // with in-neighbours) from a counter; the 32 lanes walk the target's pairs
 // j = j0, j0 + 1, ... with lane refill, one Philox block (counter
-// ((i-1)>>1, j, u, kSharedWalkKey)) per odd and following even step; per
-// source the warp accumulates meetings in shared memory and writes count and
-// score at the end of the target.  A source's own row keeps its prefilled 1.
-template <int kLayout>
+// ((i-1)>>1, j, u, kSharedWalkKey)) per odd and following even step; after
+// every step the stepping lanes' nodes are tested against their pending
+// sources (shared_meet), and lane b writes source b's count, weight sum and
+// score at the end of the target.  A source's own row
+// keeps its prefilled 1.
+template <int kLayout, bool kCoop>
 __global__ void __launch_bounds__(256, 6)
 kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
                 int32_t n_act, int32_t j0, unsigned long long *__restrict__ ctr) {
@@ -391,7 +423,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   __shared__ unsigned long long wsum[8][32];
   for (int b = threadIdx.x; b < A.k; b += blockDim.x) {
     const BatchSrc &B = A.src[b];
-    src[b] = ShSrc{B.Hj, B.wj, B.scores, B.counts, B.z, B.N_tot, B.s};
+    src[b] = ShSrc{B.wj, B.scores, B.counts, B.z, B.N_tot, B.s};
   }
   __syncthreads();
   const RoundKeys rk = round_keys(A.key0, A.key1);
@@ -400,6 +432,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   const uint32_t *M = A.M;
   const int32_t J = A.Jmax;
+  const int k = A.k;
   unsigned long long warp_steps = 0;
   for (;;) {
     int32_t q = 0;
@@ -408,12 +441,14 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     if (q >= n_act) break;
     const uint32_t u = (uint32_t)act[q];
     // sources whose own row this target is
-    const uint32_t excl = __ballot_sync(0xffffffffu, lane < A.k && src[lane].s == (int32_t)u);
-    if (lane < A.k) {
+    const uint32_t excl = __ballot_sync(0xffffffffu, lane < k && src[lane].s == (int32_t)u);
+    uint32_t c_b = 0;                // kCoop, lane b: meetings of source b at this target
+    unsigned long long w_b = 0;      // kCoop, lane b: their weight sum
+    if constexpr (!kCoop) {
       cnt[wib][lane] = 0u;
       wsum[wib][lane] = 0ull;
+      __syncwarp();
     }
-    __syncwarp();
     uint32_t deg_u = 0;
     const int32_t b_u = node_start(G, A.row_ptr, (int32_t)u, deg_u);
     uint32_t st = 0;
@@ -439,44 +474,58 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         if (next >= J) break;
         continue;  // every pair of this round was dead: take the next ones
       }
-      if (live) {
-        uint32_t x0, x1, x2, x3;
+      uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+      int32_t x = 0;
+      decltype(adj_entry(G, 0, 1, 0u, 0u)) e{};
+      // odd step i
+      bool stepped = live;
+      if (stepped) {
         philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)j, u, kSharedWalkKey, x0, x1, x2, x3);
-        auto e = adj_entry(G, b, deg, x0, x1);  // odd step i
-        int32_t x = entry_pos(G, e);
+        e = adj_entry(G, b, deg, x0, x1);
+        x = entry_pos(G, e);
         ++st;
-        pend = shared_meet(src, pend, i, j, x, cnt[wib], wsum[wib]);
+      }
+      pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
+                                  (uint32_t)(((int64_t)(i - 1) * J + j) * k), pend, j, lane,
+                                  cnt[wib], wsum[wib], c_b, w_b);
+      if (stepped) {
         pend &= M[(int64_t)i * J + j];  // still able to meet at step i + 1
         if (!pend) {
           live = false;
         } else {
           b = entry_next(G, e, x, deg);
-          if (deg == 0) {
-            live = false;
-          } else {
-            e = adj_entry(G, b, deg, x2, x3);  // even step i + 1
-            x = entry_pos(G, e);
-            ++st;
-            pend = shared_meet(src, pend, i + 1, j, x, cnt[wib], wsum[wib]);
-            pend &= M[(int64_t)(i + 1) * J + j];
-            if (!pend) {
-              live = false;
-            } else {
-              b = entry_next(G, e, x, deg);
-              if (deg == 0) live = false;
-              i += 2;
-            }
-          }
+          if (deg == 0) live = false;
+        }
+      }
+      // even step i + 1
+      stepped = live;
+      if (stepped) {
+        e = adj_entry(G, b, deg, x2, x3);
+        x = entry_pos(G, e);
+        ++st;
+      }
+      pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
+                                  (uint32_t)(((int64_t)i * J + j) * k), pend, j, lane,
+                                  cnt[wib], wsum[wib], c_b, w_b);
+      if (stepped) {
+        pend &= M[(int64_t)(i + 1) * J + j];
+        if (!pend) {
+          live = false;
+        } else {
+          b = entry_next(G, e, x, deg);
+          if (deg == 0) live = false;
+          i += 2;
         }
       }
     }
     for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(0xffffffffu, st, off);
     warp_steps += st;
     __syncwarp();
-    if (lane < A.k && !((excl >> lane) & 1u)) {
+    if (lane < k && !((excl >> lane) & 1u)) {
       const ShSrc &S = src[lane];
-      S.scores[u] = (double)wsum[wib][lane] * 2.3283064365386963e-10 / S.z;
-      if (S.counts) S.counts[u] = cnt[wib][lane];
+      const unsigned long long W = kCoop ? w_b : wsum[wib][lane];
+      S.scores[u] = (double)W * 2.3283064365386963e-10 / S.z;
+      if (S.counts) S.counts[u] = kCoop ? c_b : cnt[wib][lane];
     }
     __syncwarp();
   }
@@ -564,28 +613,31 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // The shared-walk kernel: a persistent grid of as many 256-thread blocks as
 // fit at once (ctr[0]: the target counter, cleared here; ctr[1]: the steps).
-static void launch_shared(int layout, cudaStream_t st, const BatchArgs &A, const int32_t *act,
-                          int32_t n_act, int32_t j0, unsigned long long *ctr, int dev) {
-  static int per_sm[3][64] = {};
-  auto grid = [&](const void *f, int l) {
-    int b = (dev >= 0 && dev < 64) ? per_sm[l][dev] : 0;
+static void launch_shared(int layout, bool coop, cudaStream_t st, const BatchArgs &A,
+                          const int32_t *act, int32_t n_act, int32_t j0,
+                          unsigned long long *ctr, int dev) {
+  static int per_sm[3][2][64] = {};
+  auto grid = [&](const void *f, int l, int c) {
+    int b = (dev >= 0 && dev < 64) ? per_sm[l][c][dev] : 0;
     if (!b) {
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, 0) != cudaSuccess || b < 1)
         b = 1;
-      if (dev >= 0 && dev < 64) per_sm[l][dev] = b;
+      if (dev >= 0 && dev < 64) per_sm[l][c][dev] = b;
     }
     return sm_count(dev) * b;
   };
+#define SRK_SH_LAUNCH(L, C)                                                           \
+  kb_shared_walks<L, C><<<grid((const void *)kb_shared_walks<L, C>, L, C), 256, 0, st>>>( \
+      A, act, n_act, j0, ctr)
   cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st);
-  if (layout == kWide)
-    kb_shared_walks<kWide><<<grid((const void *)kb_shared_walks<kWide>, kWide), 256, 0, st>>>(
-        A, act, n_act, j0, ctr);
-  else if (layout == kCsr)
-    kb_shared_walks<kCsr><<<grid((const void *)kb_shared_walks<kCsr>, kCsr), 256, 0, st>>>(
-        A, act, n_act, j0, ctr);
-  else
-    kb_shared_walks<kNarrow><<<grid((const void *)kb_shared_walks<kNarrow>, kNarrow), 256, 0,
-                               st>>>(A, act, n_act, j0, ctr);
+  if (layout == kWide) {
+    if (coop) SRK_SH_LAUNCH(kWide, true); else SRK_SH_LAUNCH(kWide, false);
+  } else if (layout == kCsr) {
+    if (coop) SRK_SH_LAUNCH(kCsr, true); else SRK_SH_LAUNCH(kCsr, false);
+  } else {
+    if (coop) SRK_SH_LAUNCH(kNarrow, true); else SRK_SH_LAUNCH(kNarrow, false);
+  }
+#undef SRK_SH_LAUNCH
 }
 
 static std::mutex g_stream_mu;
@@ -678,14 +730,22 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     size_t need = 0;
     int32_t i1 = i0;
     std::vector<size_t> ws_off;
+    int64_t sh_L = 1, sh_N = 0;  // shared walks: the records' extent so far
     while (i1 < k && !(shared && i1 - i0 >= 32)) {
+      if (shared) {  // the records are indexed with 32 bits
+        const int64_t L1 = std::max<int64_t>(sh_L, std::max(tabs[(size_t)i1].L, 1));
+        const int64_t N1 = std::max<int64_t>(sh_N, tabs[(size_t)i1].N_tot);
+        if (i1 > i0 && L1 * N1 * (i1 - i0 + 1) >= ((int64_t)1 << 31)) break;
+        sh_L = L1;
+        sh_N = N1;
+      }
       Workspace w;
       const QueryTab &t1 = tabs[(size_t)i1];
       const size_t b = align256(plan(t1, &w, nullptr)) +
                        (d_scores ? 0 : align256(8 * n)) + (d_counts ? 0 : align256(4 * n)) +
                        (shared ? align256(4 * (size_t)std::max(t1.L, 1) * t1.N_tot) +
                                      align256(8 * (size_t)t1.N_tot)
-                               : 0);
+                               : 0);  // (an upper bound of the source's share of the records)
       if (i1 > i0 && need + b > budget) break;
       ws_off.push_back(need);
       need += b;
@@ -700,12 +760,21 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       Jmax = std::max(Jmax, t.N_tot);
       j0 = std::min(j0, t.L >= 1 ? t.P[1] : t.N_tot);  // below, every pair has length 0
     }
-    // shared walks: the step masks, Lmax + 1 rows of Jmax words
+    // shared walks: the warp-cooperative meeting test pays off when a pair is
+    // pending for several sources at once (an average of 4 or more at the
+    // first step, counting a source's pairs as pending up to its N_tot)
+    double pend_avg = 0.0;
+    for (int32_t b = i0; b < i1; ++b) pend_avg += (double)tabs[(size_t)b].N_tot / (double)Jmax;
+    const bool coop = pend_avg >= 4.0;
+    // shared walks: the step masks, Lmax + 1 rows of Jmax words, and the
+    // records, Lmax x Jmax x kb words
     const size_t m_bytes = shared ? 4 * (size_t)(Lmax + 1) * (size_t)Jmax : 0;
+    const size_t h_bytes = shared ? 4 * (size_t)std::max(Lmax, 1) * (size_t)Jmax * kb : 0;
     const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
                         align256(sizeof(int64_t) * (kb + 1)) +
                         align256(sizeof(int32_t) * (kb + 1)) +
-                        align256(sizeof(unsigned long long) * (kb + 2)) + align256(m_bytes);
+                        align256(sizeof(unsigned long long) * (kb + 2)) + align256(m_bytes) +
+                        align256(h_bytes);
     char *base = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&base, head + need, mp, st);
     if (e != cudaSuccess) { rc = cuda_fail(e, "batch workspace allocation"); break; }
@@ -716,6 +785,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     unsigned long long *d_ctr = (unsigned long long *)((char *)d_act_src +
                                                          align256(sizeof(int32_t) * (kb + 1)));
     uint32_t *d_M = (uint32_t *)((char *)d_ctr + align256(sizeof(unsigned long long) * (kb + 2)));
+    int32_t *d_H = (int32_t *)((char *)d_M + align256(m_bytes));
     // d_ctr[0] = item counter, d_ctr[1 + i] = steps of source i; n_act_src in d_act_src[kb]
     char *ws_base = base + head;
     std::vector<BatchSrc> hsrc((size_t)kb);
@@ -733,11 +803,8 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       S.counts = !meet_counts ? nullptr
                  : (d_counts ? meet_counts + (size_t)(i0 + b) * n : (uint32_t *)extra);
       if (meet_counts && !d_counts) extra += align256(4 * n);
-      S.Hj = nullptr;
       S.wj = nullptr;
       if (shared) {
-        S.Hj = (int32_t *)extra;
-        extra += align256(4 * (size_t)std::max(t.L, 1) * t.N_tot);
         S.wj = (unsigned long long *)extra;
         extra += align256(8 * (size_t)t.N_tot);
       }
@@ -772,6 +839,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     A.key0 = (uint32_t)seed;
     A.key1 = (uint32_t)(seed >> 32);
     A.M = d_M;
+    A.H = d_H;
     A.Jmax = Jmax;
     const int gw = (int)std::max<int64_t>(1, std::min<int64_t>((A.total_walks + 255) / 256,
                                                                 (int64_t)sms * 8));
@@ -843,7 +911,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     auto enqueue_all = [&](cudaStream_t s2) {
       enqueue_source_side(s2);
       if (shared)
-        launch_shared(g->layout, s2, A, g->act, g->n_act, j0, d_ctr, dev);
+        launch_shared(g->layout, coop, s2, A, g->act, g->n_act, j0, d_ctr, dev);
       else
         launch_targets(g->layout, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
                        d_ctr, INT64_MAX, Lmax);
