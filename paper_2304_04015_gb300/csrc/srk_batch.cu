@@ -692,6 +692,21 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     int rc = build_table(g->n, sources[i], c, eps[i], seed, opt, &tabs[i]);
     if (rc) return fail(rc, "source %d (index %d): %s", sources[i], i, srk_last_error());
   }
+  // batch position -> the caller's row.  With shared target walks the
+  // sources are grouped by walk budget (N_tot, then L), so that a batch's
+  // sources share as many pairs as possible; a source's results do not
+  // depend on its batch, since its target walks do not depend on it.
+  std::vector<int32_t> row_of((size_t)k);
+  for (int32_t i = 0; i < k; ++i) row_of[(size_t)i] = i;
+  if (shared) {
+    std::stable_sort(row_of.begin(), row_of.end(), [&](int32_t a, int32_t b) {
+      const QueryTab &ta = tabs[(size_t)a], &tb = tabs[(size_t)b];
+      return ta.N_tot != tb.N_tot ? ta.N_tot < tb.N_tot : ta.L < tb.L;
+    });
+    std::vector<QueryTab> sorted((size_t)k);
+    for (int32_t p = 0; p < k; ++p) sorted[(size_t)p] = tabs[(size_t)row_of[(size_t)p]];
+    tabs.swap(sorted);
+  }
   DeviceGuard guard(g->device);
   const int dev = g->device;
   const int sms = sm_count(dev);
@@ -798,10 +813,11 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       const size_t core = align256(plan(t, &S.w, wb));
       char *extra = wb + core;
       S.tab = d_tab + b;
-      S.scores = d_scores ? scores + (size_t)(i0 + b) * n : (double *)extra;
+      const size_t row = (size_t)row_of[(size_t)(i0 + b)];
+      S.scores = d_scores ? scores + row * n : (double *)extra;
       if (!d_scores) extra += align256(8 * n);
       S.counts = !meet_counts ? nullptr
-                 : (d_counts ? meet_counts + (size_t)(i0 + b) * n : (uint32_t *)extra);
+                 : (d_counts ? meet_counts + row * n : (uint32_t *)extra);
       if (meet_counts && !d_counts) extra += align256(4 * n);
       S.wj = nullptr;
       if (shared) {
@@ -961,10 +977,10 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     for (int32_t b = 0; b < kb && e == cudaSuccess; ++b) {
       const BatchSrc &S = hsrc[(size_t)b];
       if (!d_scores)
-        e = cudaMemcpyAsync(scores + (size_t)(i0 + b) * n, S.scores, 8 * n,
+        e = cudaMemcpyAsync(scores + (size_t)row_of[(size_t)(i0 + b)] * n, S.scores, 8 * n,
                             cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess && meet_counts && !d_counts)
-        e = cudaMemcpyAsync(meet_counts + (size_t)(i0 + b) * n, S.counts, 4 * n,
+        e = cudaMemcpyAsync(meet_counts + (size_t)row_of[(size_t)(i0 + b)] * n, S.counts, 4 * n,
                             cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess && opt && opt->stats) {

@@ -196,11 +196,13 @@ k_topk_collect(const double *__restrict__ rows, int64_t n, const int32_t *__rest
 __global__ void __launch_bounds__(1024)
 k_topk_sort(const RowSel *__restrict__ sel, int32_t top, int32_t P,
             const unsigned long long *__restrict__ in_key, const int32_t *__restrict__ in_id,
-            int32_t *__restrict__ top_nodes, double *__restrict__ top_scores,
-            int32_t *__restrict__ top_count, int64_t *__restrict__ nnz_out) {
+            const int32_t *__restrict__ dst_row, int32_t *__restrict__ top_nodes,
+            double *__restrict__ top_scores, int32_t *__restrict__ top_count,
+            int64_t *__restrict__ nnz_out) {
   extern __shared__ unsigned long long smk[];
   int32_t *smi = reinterpret_cast<int32_t *>(smk + P);
   const int r = blockIdx.x;
+  const int64_t d = dst_row[r];  // the caller's row of this chunk row
   const RowSel S = sel[r];
   const int cnt = (int)std::min<int64_t>(S.nnz, (int64_t)top);
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -235,12 +237,12 @@ k_topk_sort(const RowSel *__restrict__ sel, int32_t top, int32_t P,
     }
   }
   for (int i = threadIdx.x; i < top; i += blockDim.x) {
-    top_nodes[(int64_t)r * top + i] = i < cnt ? smi[i] : -1;
-    top_scores[(int64_t)r * top + i] = i < cnt ? __longlong_as_double((long long)smk[i]) : 0.0;
+    top_nodes[d * top + i] = i < cnt ? smi[i] : -1;
+    top_scores[d * top + i] = i < cnt ? __longlong_as_double((long long)smk[i]) : 0.0;
   }
   if (threadIdx.x == 0) {
-    if (top_count) top_count[r] = cnt;
-    if (nnz_out) nnz_out[r] = S.nnz;
+    if (top_count) top_count[d] = cnt;
+    if (nnz_out) nnz_out[d] = S.nnz;
   }
 }
 
@@ -284,13 +286,12 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
   const size_t b_rows = al(8 * (size_t)R * n), b_sel = al(sizeof(RowSel) * R),
                b_hist = al(4 * 256 * (size_t)R), b_ties = al(4 * (size_t)R * n_chunks),
                b_key = al(8 * (size_t)R * top), b_id = al(4 * (size_t)R * top),
-               b_src = al(4 * (size_t)R);
+               b_src = al(4 * (size_t)R), b_dst = al(4 * (size_t)R);
   cudaMemPool_t mp = pool(g->device);
   if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
   char *base = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync((void **)&base,
-                                          b_rows + b_sel + b_hist + b_ties + b_key + b_id + b_src,
-                                          mp, st);
+  cudaError_t e = cudaMallocFromPoolAsync(
+      (void **)&base, b_rows + b_sel + b_hist + b_ties + b_key + b_id + b_src + b_dst, mp, st);
   if (e != cudaSuccess) return cuda_fail(e, "srk_multi_source_topk: scratch");
   double *rows = (double *)base;
   RowSel *sel = (RowSel *)(base + b_rows);
@@ -299,6 +300,21 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
   unsigned long long *skey = (unsigned long long *)((char *)ties + b_ties);
   int32_t *sid = (int32_t *)((char *)skey + b_key);
   int32_t *dsrc = (int32_t *)((char *)sid + b_id);
+  int32_t *ddst = (int32_t *)((char *)dsrc + b_src);
+  // the order the sources run in: as given, or grouped by eps (descending,
+  // so by walk budget) when they share target walks, so that a chunk's
+  // batches share as many pairs as possible
+  std::vector<int32_t> order((size_t)k);
+  for (int32_t i = 0; i < k; ++i) order[(size_t)i] = i;
+  if (opt && (opt->flags & SRK_OPT_SHARED_WALKS))
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return eps[a] > eps[b]; });
+  std::vector<int32_t> src_o((size_t)k);
+  std::vector<double> eps_o((size_t)k);
+  for (int32_t i = 0; i < k; ++i) {
+    src_o[(size_t)i] = sources[order[(size_t)i]];
+    eps_o[(size_t)i] = eps[order[(size_t)i]];
+  }
   int rc = SRK_OK;
   srk_stats total;
   memset(&total, 0, sizeof total);
@@ -313,7 +329,8 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
   for (int32_t i0 = 0; i0 < k && rc == SRK_OK; i0 += R) {
     const int32_t r = std::min(R, k - i0);
     o.stats = (opt && opt->stats) ? &part : nullptr;
-    rc = srk_multi_source(g, sources + i0, r, c, eps + i0, seed, &o, rows, nullptr, st);
+    rc = srk_multi_source(g, src_o.data() + i0, r, c, eps_o.data() + i0, seed, &o, rows, nullptr,
+                          st);
     if (rc) break;
     if (opt && opt->stats) {
       total.source_steps += part.source_steps;
@@ -332,8 +349,10 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
     }
     if ((e = cudaMemcpyAsync(sel, h.data(), sizeof(RowSel) * r, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess ||
-        (e = cudaMemcpyAsync(dsrc, sources + i0, 4 * (size_t)r, cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess ||
+        (e = cudaMemcpyAsync(dsrc, src_o.data() + i0, 4 * (size_t)r, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(ddst, order.data() + i0, 4 * (size_t)r, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
         (e = cudaMemsetAsync(hist, 0, 4 * 256 * (size_t)r, st)) != cudaSuccess) {
       rc = cuda_fail(e, "srk_multi_source_topk: row state");
       break;
@@ -355,10 +374,8 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
       rc = cuda_fail(e, "srk_multi_source_topk: sort shared memory");
       break;
     }
-    k_topk_sort<<<r, 1024, smem, st>>>(sel, top, P, skey, sid, top_nodes + (int64_t)i0 * top,
-                                        top_scores + (int64_t)i0 * top,
-                                        top_count ? top_count + i0 : nullptr,
-                                        nnz ? nnz + i0 : nullptr);
+    k_topk_sort<<<r, 1024, smem, st>>>(sel, top, P, skey, sid, ddst, top_nodes, top_scores,
+                                        top_count, nnz);
     e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "srk_multi_source_topk: selection");
   }

@@ -57,8 +57,8 @@ def run_topk(srk, g, n, sources, eps, seed, top, **kw):
             dense.cpu().numpy())
 
 
-@pytest.mark.parametrize("top", [1, 64, 4096])
-def test_topk_equals_dense_order_statistics(srk, top):
+@pytest.mark.parametrize("top,shared", [(1, False), (64, False), (4096, False), (64, True)])
+def test_topk_equals_dense_order_statistics(srk, top, shared):
     import torch
     dev = torch.device("cuda:0")
     rp, col = rmat_graph(16)
@@ -70,7 +70,8 @@ def test_topk_equals_dense_order_statistics(srk, top):
     eps = [0.05, 0.1, 0.05, 0.1, 0.08]
     g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
     try:
-        tn, ts, tc, nz, dense = run_topk(srk, g, n, sources, eps, 5, top)
+        # with shared walks the sources run grouped by eps; rows must land in place
+        tn, ts, tc, nz, dense = run_topk(srk, g, n, sources, eps, 5, top, shared_walks=shared)
         en, es, ec, ez = expected_topk(dense, sources, top)
         assert np.array_equal(tc, ec) and np.array_equal(nz, ez)
         assert np.array_equal(tn, en) and np.array_equal(ts, es)
