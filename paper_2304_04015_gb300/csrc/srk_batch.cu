@@ -50,10 +50,10 @@ struct BatchArgs {
   const int32_t *npos;
   int32_t pos_bits;
   uint32_t key0, key1;
-  uint2 *M;       // shared walks: M[(i-1) Jmax + j].x bit b = pair j of batch source
-                  // b may still meet at step i (cap_b(j) >= i); .y = the signature
-                  // of those sources' nodes at step i (bit node_hash(node) per
-                  // node); Lmax + 1 rows
+  uint4 *M;       // shared walks: M[(i-1) Jmax + j].x bit b = pair j of batch source
+                  // b may still meet at step i (cap_b(j) >= i); (.y, .z) = the
+                  // 64-bit signature of those sources' nodes at step i (bit
+                  // node_hash(node) per node); Lmax + 1 rows
   int32_t *H;     // shared walks: H[((i-1) Jmax + j) k + b] = node of source b's walk
                   // sigma_b(j) at step i, for i <= cap_b(j): one record per (step, pair)
   int32_t Jmax;   // shared walks: the largest N_tot of the batch
@@ -333,10 +333,15 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
 // every pending source reads one line.  Batches hold at most 32 sources (one
 // mask bit each).
 
-// One of 32 bits for a node: the signature of a (step, pair) record has the
+// One of 64 bits for a node: the signature of a (step, pair) record has the
 // bits of its nodes, so a walk whose node's bit is clear meets no source there.
 __device__ __forceinline__ uint32_t node_hash(int32_t x) {
-  return ((uint32_t)x * 0x9E3779B9u) >> 27;
+  return ((uint32_t)x * 0x9E3779B9u) >> 26;
+}
+// Is the bit of node x set in the signature (lo, hi)?
+__device__ __forceinline__ bool sig_has(uint32_t lo, uint32_t hi, int32_t x) {
+  const uint32_t h = node_hash(x);
+  return ((h < 32 ? lo : hi) >> (h & 31)) & 1u;
 }
 
 // Per source and pair j: the pair's weight, its hit-table column (steps
@@ -355,9 +360,10 @@ __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
     const uint32_t bit = 1u << i_;
     for (int q = 1; q <= cap; ++q) {
       A.H[((int64_t)(q - 1) * A.Jmax + j) * A.k + i_] = sp[q - 1];
-      uint2 *cell = &A.M[(int64_t)(q - 1) * A.Jmax + j];
+      uint4 *cell = &A.M[(int64_t)(q - 1) * A.Jmax + j];
+      const uint32_t h = node_hash(sp[q - 1]);
       atomicOr(&cell->x, bit);
-      atomicOr(&cell->y, 1u << node_hash(sp[q - 1]));
+      atomicOr(h < 32 ? &cell->y : &cell->z, 1u << (h & 31));
     }
   })
 }
@@ -380,17 +386,18 @@ struct ShSrc {
 // compares the node of source b's walk, H[r_l + b], with x_l, so one
 // coalesced line serves all of lane l's sources, and lane b counts source
 // b's meetings in registers (c_b, w_b).  A lane whose node's bit is clear in
-// the step's signature `sig` skips the test.  Returns the sources that met on
+// the step's signature (sig_lo, sig_hi) skips the test.  Returns the sources that met on
 // this lane's own pair.
 template <bool kCoop>
 __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t *H, int k,
                                                 bool stepped, int32_t x, uint32_t rec,
-                                                uint32_t pend, uint32_t sig, int32_t j, int lane,
+                                                uint32_t pend, uint32_t sig_lo, uint32_t sig_hi,
+                                                int32_t j, int lane,
                                                 uint32_t *cnt, unsigned long long *wsum,
                                                 uint32_t &c_b, unsigned long long &w_b) {
   uint32_t mine = 0u;
   if constexpr (!kCoop) {
-    if (stepped && ((sig >> node_hash(x)) & 1u))
+    if (stepped && sig_has(sig_lo, sig_hi, x))
       for (uint32_t m = pend; m; m &= m - 1) {
         const int b = __ffs(m) - 1;
         if (H[rec + (uint32_t)b] == x) {
@@ -400,7 +407,7 @@ __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t 
         }
       }
   } else {
-    const bool maybe = stepped && pend != 0u && ((sig >> node_hash(x)) & 1u);
+    const bool maybe = stepped && pend != 0u && sig_has(sig_lo, sig_hi, x);
     for (uint32_t m = __ballot_sync(0xffffffffu, maybe); m; m &= m - 1) {
       const int l = __ffs(m) - 1;
       const int32_t xl = __shfl_sync(0xffffffffu, x, l);
@@ -443,7 +450,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanes_below = (1u << lane) - 1u;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
-  const uint2 *M = A.M;
+  const uint4 *M = A.M;
   const int32_t J = A.Jmax;
   const int k = A.k;
   unsigned long long warp_steps = 0;
@@ -467,16 +474,17 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     uint32_t st = 0;
     int32_t next = j0, j = 0, i = 1, b = 0;
     bool live = false;
-    uint32_t deg = 0, pend = 0, sig = 0;
+    uint32_t deg = 0, pend = 0, sig_lo = 0, sig_hi = 0;
     for (;;) {
       const uint32_t idle = __ballot_sync(0xffffffffu, !live);
       if (idle) {
         if (!live) {
           j = next + __popc(idle & lanes_below);
           if (j < J) {
-            const uint2 m1 = M[j];
+            const uint4 m1 = M[j];
             pend = m1.x & ~excl;
-            sig = m1.y;
+            sig_lo = m1.y;
+            sig_hi = m1.z;
             live = pend != 0u;
             i = 1;
             b = b_u;
@@ -501,12 +509,13 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         ++st;
       }
       pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
-                                  (uint32_t)(((int64_t)(i - 1) * J + j) * k), pend, sig, j, lane,
+                                  (uint32_t)(((int64_t)(i - 1) * J + j) * k), pend, sig_lo, sig_hi, j, lane,
                                   cnt[wib], wsum[wib], c_b, w_b);
       if (stepped) {
-        const uint2 mn = M[(int64_t)i * J + j];  // still able to meet at step i + 1
+        const uint4 mn = M[(int64_t)i * J + j];  // still able to meet at step i + 1
         pend &= mn.x;
-        sig = mn.y;
+        sig_lo = mn.y;
+        sig_hi = mn.z;
         if (!pend) {
           live = false;
         } else {
@@ -522,12 +531,13 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         ++st;
       }
       pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
-                                  (uint32_t)(((int64_t)i * J + j) * k), pend, sig, j, lane,
+                                  (uint32_t)(((int64_t)i * J + j) * k), pend, sig_lo, sig_hi, j, lane,
                                   cnt[wib], wsum[wib], c_b, w_b);
       if (stepped) {
-        const uint2 mn = M[(int64_t)(i + 1) * J + j];
+        const uint4 mn = M[(int64_t)(i + 1) * J + j];
         pend &= mn.x;
-        sig = mn.y;
+        sig_lo = mn.y;
+        sig_hi = mn.z;
         if (!pend) {
           live = false;
         } else {
@@ -803,7 +813,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     // shared walks: the step masks and signatures, Lmax + 1 rows of Jmax
     // pairs of words, and the
     // records, Lmax x Jmax x kb words
-    const size_t m_bytes = shared ? 8 * (size_t)(Lmax + 1) * (size_t)Jmax : 0;
+    const size_t m_bytes = shared ? 16 * (size_t)(Lmax + 1) * (size_t)Jmax : 0;
     const size_t h_bytes = shared ? 4 * (size_t)std::max(Lmax, 1) * (size_t)Jmax * kb : 0;
     const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
                         align256(sizeof(int64_t) * (kb + 1)) +
@@ -819,7 +829,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     int32_t *d_act_src = (int32_t *)((char *)d_off + align256(sizeof(int64_t) * (kb + 1)));
     unsigned long long *d_ctr = (unsigned long long *)((char *)d_act_src +
                                                          align256(sizeof(int32_t) * (kb + 1)));
-    uint2 *d_M = (uint2 *)((char *)d_ctr + align256(sizeof(unsigned long long) * (kb + 2)));
+    uint4 *d_M = (uint4 *)((char *)d_ctr + align256(sizeof(unsigned long long) * (kb + 2)));
     int32_t *d_H = (int32_t *)((char *)d_M + align256(m_bytes));
     // d_ctr[0] = item counter, d_ctr[1 + i] = steps of source i; n_act_src in d_act_src[kb]
     char *ws_base = base + head;
