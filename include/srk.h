@@ -20,9 +20,18 @@
  *   (Eq. 1).  A walk moves from v to a uniform member of I(v), i.e. along a
  *   reversed edge (the graph G-bar of Lemma 2).  The list order matters only
  *   for reproducibility: the k-th entry is chosen by index.
- * Random numbers: Philox4x32-10 keyed by (seed mod 2^32, seed >> 32); the
- *   counter of walk r of node v for query source s at step i >= 1 is
- *   ((i-1) >> 1, r, v, s), so every walk is reproducible on its own.
+ * Random numbers (Salmon et al., SC'11): walk steps use Philox2x32-10 with
+ *   the 32-bit walk key kappa(seed, q) = h32(q ^ (mix64(seed) mod 2^32))
+ *   (mix64: SplitMix64's output function; h32: the "lowbias32" finalizer;
+ *   q = the query source s); step i >= 1 of walk replica r from node v takes
+ *   word (i-1) & 1 of the block with counter (((i-1) >> 1) 2^24 + r, v), and
+ *   the in-neighbour index below d is Lemire's bounded draw of that word
+ *   (floor(w d / 2^32), accepted when w d mod 2^32 >= 2^32 mod d; a rejected
+ *   word, probability < d / 2^32, is replaced by floor(R d / 2^64) from the
+ *   block whose counter has the top bit of word (i-1) & 1 set), so every walk
+ *   is reproducible on its own and every index is uniform up to d / 2^64.
+ *   The source's Fisher-Yates draws use Philox4x32-10 keyed by
+ *   (seed mod 2^32, seed >> 32).
  * Errors: every function returns SRK_OK (0) or a negative code; the message
  *   of the last failure on the calling thread is srk_last_error().  On error
  *   no output is guaranteed to be written.
@@ -74,9 +83,9 @@ extern "C" {
                                   3.6x slower than the default pairing */
 
 #define SRK_OPT_SHARED_WALKS 8  /* target walks keyed by (node, replica) alone:
-                                  walk r of target u draws step i from the
-                                  Philox counter ((i-1)>>1, r, u, 0xFFFFFFFE)
-                                  instead of ((i-1)>>1, r, u, s), so every
+                                  walk r of target u draws its steps under the
+                                  walk key kappa(seed, 0xFFFFFFFE) instead of
+                                  kappa(seed, s), so every
                                   node's walks are the same for all sources,
                                   as Algorithm 1 draws each node's walks once.
                                   Each (s, u) estimate keeps its law; estimates
@@ -190,7 +199,7 @@ int srk_graph_layout(const srk_graph *g, int32_t *layout);
  *   c     : SimRank decay factor, 0 < c < 1 (walks continue w.p. sqrt(c)).
  *   eps   : absolute error target, 3/n^p < eps < 1 (Theorem 6); z =
  *           ln(2n^q) / (2 (eps - 3/n^p)^2) walk samples per node.
- *   seed  : 64-bit Philox key.
+ *   seed  : 64-bit seed of every random draw of the query.
  *   opt   : NULL or options (see srk_opts).
  *   scores      : n FP64 outputs, s~(s, u) = W_u 2^-32 / z, s~(s, s) = 1, and
  *                 0 for a node without in-neighbours.
@@ -221,7 +230,7 @@ int srk_single_source(const srk_graph *g, int32_t s, double c, double eps,
  *   scores  : k x n FP64 outputs (host or device), row i for sources[i].
  *   meet_counts : NULL or k x n uint32 outputs.
  * Results equal k calls of srk_single_source with the same seed (each walk's
- * Philox counter contains its source).  The sources run in batches sized by
+ * key is derived from its source).  The sources run in batches sized by
  * a scratch budget (a quarter of free device memory, at most 8 GiB, or the
  * byte count in the environment variable SRK_BATCH_BYTES): one
  * launch per source-side phase for the whole batch, then one persistent

@@ -20,23 +20,37 @@
  *       pair counts once (Section 5.5) and adds the Lemma 7 weight of its two
  *       lengths, quantised to 2^-32 units and passed in by the caller.
  *
- * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
- * numbers: as easy as 1, 2, 3", SC'11), restated from that paper's definition:
- * ten rounds of two 32x32->64 multiplies by 0xD2511F53 and 0xCD9E8D57 with the
- * key bumped by the Weyl constants 0x9E3779B9 and 0xBB67AE85 between rounds.
- *   key     = (seed mod 2^32, seed >> 32)
- *   walk r of node v for query source s, step i >= 1:
- *           counter = ((i-1) >> 1, r, v, s); the 64-bit draw is word
- *           2*((i-1)&1) (high half) and word 2*((i-1)&1)+1 (low half)
- *   Fisher-Yates draw t: counter = (t >> 1, 0xFFFFFFFF, 0xFFFFFFFF, s),
- *           words 2*(t&1) (high) and 2*(t&1)+1 (low)
- *   uniform index below d from a 64-bit draw R: floor(R * d / 2^64).
+ * Random numbers: two generators of Salmon, Moraes, Dror, Shaw ("Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11), restated from that paper's
+ * definitions.  Philox4x32-10: ten rounds of two 32x32->64 multiplies by
+ * 0xD2511F53 and 0xCD9E8D57, the two key words bumped by the Weyl constants
+ * 0x9E3779B9 and 0xBB67AE85 between rounds.  Philox2x32-10: ten rounds of one
+ * multiply by 0xD256D193, (x0, x1) -> (hi ^ k ^ x1, lo), the 32-bit key
+ * bumped by 0x9E3779B9 between rounds.
+ *   Fisher-Yates draw t (Philox4x32-10, key (seed mod 2^32, seed >> 32)):
+ *           counter (t >> 1, 0xFFFFFFFF, 0xFFFFFFFF, s), words 2*(t&1) (high)
+ *           and 2*(t&1)+1 (low) form R; k_t = floor(R * (t+1) / 2^64).
+ *   walks (Philox2x32-10): the walk key of word q is
+ *           kappa(seed, q) = h32(q ^ (mix64(seed) mod 2^32))
+ *           (h32 and mix64 below; q = s: the source's walks, and its target
+ *           walks by default).  Step i >= 1 of walk replica r from node v
+ *           takes word (i-1)&1 of the block with counter
+ *           (((i-1) >> 1) * 2^24 + r, v), w.  The in-neighbour index below
+ *           d is Lemire's bounded draw (D. Lemire, "Fast random integer
+ *           generation in an interval", ACM TOMACS 2019): floor(w d / 2^32)
+ *           when (w d mod 2^32) >= (2^32 mod d), which gives every index
+ *           exactly floor(2^32 / d) of the 2^32 words; otherwise (probability
+ *           below d / 2^32) floor(R d / 2^64) with R = (y0 * 2^32 + y1) from
+ *           the block of counter (c0 + 2^31, v) for an odd step and
+ *           (c0, v + 2^31) for an even one (r < 2^24, i <= 255 and v < 2^31,
+ *           so these never name a step's own block).  The index is uniform
+ *           up to d / 2^64.
  *
  * Optional shared target walks (Algorithm 1 draws every node's walks once,
- * whatever the query): walk r of a target v is then keyed by (v, r) alone,
- * counter ((i-1) >> 1, r, v, 0xFFFFFFFE), so the walks of v are the same for
- * every source and a batch of sources can share them.  Source walks keep the
- * counter ((i-1) >> 1, r, s, s) (s < 2^31, so the two never coincide).
+ * whatever the query): target walks then take the key kappa(seed,
+ * 0xFFFFFFFE), so the walks of v are the same for every source and a batch of
+ * sources can share them; source walks keep kappa(seed, s) (s < 2^31 and
+ * kappa is injective in q, so the two keys differ).
  *
  * Optional literal shuffle of the targets' walks (every node's walks are
  * shuffled in Section 5.2; the default shuffles only the source's): target u
@@ -71,6 +85,7 @@
 #define PHILOX_M1 0xCD9E8D57u
 #define PHILOX_W0 0x9E3779B9u
 #define PHILOX_W1 0xBB67AE85u
+#define PHILOX2_M 0xD256D193u
 
 void srko_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                         uint32_t out[4]) {
@@ -90,6 +105,18 @@ void srko_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+void srko_philox2x32_10(const uint32_t ctr[2], uint32_t key, uint32_t out[2]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], k = key;
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p = (uint64_t)PHILOX2_M * x0;
+        uint32_t hi = (uint32_t)(p >> 32), lo = (uint32_t)p;
+        x0 = hi ^ k ^ x1;
+        x1 = lo;
+        k += PHILOX_W0;
+    }
+    out[0] = x0; out[1] = x1;
+}
+
 /* floor(r * d / 2^64): a uniform index in [0, d) from a 64-bit draw. */
 uint32_t srko_index(uint64_t r, uint32_t d) {
     return (uint32_t)(((unsigned __int128)r * d) >> 64);
@@ -104,25 +131,8 @@ static uint64_t draw64(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
     return ((uint64_t)w[2 * half] << 32) | w[2 * half + 1];
 }
 
-/* Counter word of the shared target walks, as a signed 32-bit value. */
+/* Key word of the shared target walks, as a signed 32-bit value. */
 #define SRKO_SHARED_KEY ((int32_t)-2)
-
-/* One walk of nominal length `len` from v, replica r, query source s.
- * Writes the node at step i to pos[i-1]; returns the number of steps taken
- * (smaller than len only when a node without in-neighbours was reached). */
-int srko_walk(const int32_t *row_ptr, const int32_t *col, int32_t v,
-              int32_t r, int32_t s, uint64_t seed, int len, int32_t *pos) {
-    int32_t x = v;
-    for (int i = 1; i <= len; ++i) {
-        int32_t beg = row_ptr[x], deg = row_ptr[x + 1] - row_ptr[x];
-        if (deg == 0) return i - 1;
-        uint64_t R = draw64((uint32_t)((i - 1) >> 1), (uint32_t)r,
-                            (uint32_t)v, (uint32_t)s, seed, (i - 1) & 1);
-        x = col[beg + srko_index(R, (uint32_t)deg)];
-        pos[i - 1] = x;
-    }
-    return len;
-}
 
 static uint64_t mix64(uint64_t z) {
     z ^= z >> 30;
@@ -140,6 +150,49 @@ static uint32_t h32(uint32_t x) {
     x *= 0x846CA68Bu;
     x ^= x >> 16;
     return x;
+}
+
+/* kappa(seed, q): the Philox2x32-10 key of the walks of key word q. */
+uint32_t srko_walk_key(uint64_t seed, uint32_t q) {
+    return h32(q ^ (uint32_t)mix64(seed));
+}
+
+/* Lemire's bounded draw of an index in [0, d) from the 32-bit word w, with
+ * the 64-bit draw r standing in when w is rejected. */
+uint32_t srko_bounded(uint32_t w, uint32_t d, uint64_t r) {
+    uint64_t m = (uint64_t)w * d;
+    uint32_t low = (uint32_t)m;
+    uint32_t threshold = (uint32_t)(((uint64_t)1 << 32) % d);
+    if (low >= threshold) return (uint32_t)(m >> 32);
+    return srko_index(r, d);
+}
+
+/* The in-neighbour index below d of step i of walk replica r from v. */
+uint32_t srko_step_index(uint32_t key, int i, uint32_t r, uint32_t v, uint32_t d) {
+    uint32_t c0 = ((uint32_t)(i - 1) >> 1) * 16777216u + r;
+    uint32_t ctr[2] = {c0, v}, w[2];
+    srko_philox2x32_10(ctr, key, w);
+    int odd = ((i - 1) & 1) == 0;
+    uint32_t alt[2] = {odd ? c0 + 2147483648u : c0, odd ? v : v + 2147483648u}, y[2];
+    srko_philox2x32_10(alt, key, y);
+    return srko_bounded(w[(i - 1) & 1], d, ((uint64_t)y[0] << 32) | y[1]);
+}
+
+/* One walk of nominal length `len` from v, replica r, key word q (the query
+ * source, or SRKO_SHARED_KEY).  Writes the node at step i to pos[i-1];
+ * returns the number of steps taken (smaller than len only when a node
+ * without in-neighbours was reached). */
+int srko_walk(const int32_t *row_ptr, const int32_t *col, int32_t v,
+              int32_t r, int32_t q, uint64_t seed, int len, int32_t *pos) {
+    uint32_t key = srko_walk_key(seed, (uint32_t)q);
+    int32_t x = v;
+    for (int i = 1; i <= len; ++i) {
+        int32_t beg = row_ptr[x], deg = row_ptr[x + 1] - row_ptr[x];
+        if (deg == 0) return i - 1;
+        x = col[beg + srko_step_index(key, i, (uint32_t)r, (uint32_t)v, (uint32_t)deg)];
+        pos[i - 1] = x;
+    }
+    return len;
 }
 
 /* pi_u(j): the keyed permutation of the literal target shuffle (see above). */

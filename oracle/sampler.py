@@ -46,6 +46,15 @@ def lib():
         L.srko_philox4x32_10.restype = None
         L.srko_index.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
         L.srko_index.restype = ctypes.c_uint32
+        L.srko_philox2x32_10.argtypes = [u32p, ctypes.c_uint32, u32p]
+        L.srko_philox2x32_10.restype = None
+        L.srko_walk_key.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+        L.srko_walk_key.restype = ctypes.c_uint32
+        L.srko_bounded.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64]
+        L.srko_bounded.restype = ctypes.c_uint32
+        L.srko_step_index.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32,
+                                      ctypes.c_uint32, ctypes.c_uint32]
+        L.srko_step_index.restype = ctypes.c_uint32
         L.srko_walk.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.c_int32, ctypes.c_uint64, ctypes.c_int, i32p]
         L.srko_walk.restype = ctypes.c_int
@@ -80,11 +89,34 @@ def philox4x32_10(ctr, key):
     return [int(x) for x in out]
 
 
+def philox2x32_10(ctr, key: int):
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    out = np.zeros(2, dtype=np.uint32)
+    lib().srko_philox2x32_10(_ptr(c, ctypes.c_uint32), ctypes.c_uint32(key),
+                             _ptr(out, ctypes.c_uint32))
+    return [int(x) for x in out]
+
+
 def index(r: int, d: int) -> int:
     return int(lib().srko_index(ctypes.c_uint64(r), ctypes.c_uint32(d)))
 
 
-# Counter word that keys the shared target walks in place of the source.
+def walk_key(seed: int, q: int) -> int:
+    """kappa(seed, q), the Philox2x32-10 key of the walks of key word q."""
+    return int(lib().srko_walk_key(ctypes.c_uint64(seed), ctypes.c_uint32(q & 0xFFFFFFFF)))
+
+
+def bounded(w: int, d: int, r: int) -> int:
+    """Lemire's bounded draw below d from the word w (r when w is rejected)."""
+    return int(lib().srko_bounded(ctypes.c_uint32(w), ctypes.c_uint32(d), ctypes.c_uint64(r)))
+
+
+def step_index(key: int, i: int, r: int, v: int, d: int) -> int:
+    return int(lib().srko_step_index(ctypes.c_uint32(key), i, ctypes.c_uint32(r),
+                                     ctypes.c_uint32(v), ctypes.c_uint32(d)))
+
+
+# Key word of the shared target walks in place of the source.
 SHARED_KEY = -2
 
 

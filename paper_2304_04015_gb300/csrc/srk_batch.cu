@@ -50,6 +50,7 @@ struct BatchArgs {
   const int32_t *npos;
   int32_t pos_bits;
   uint32_t key0, key1;
+  uint32_t shared_key;  // walk key of the shared target walks
   uint4 *M;       // shared walks: M[(i-1) Jmax + j].x bit b = pair j of batch source
                   // b may still meet at step i (cap_b(j) >= i); (.y, .z) = the
                   // 64-bit signature of those sources' nodes at step i (bit
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(256) kb_source_walks(const __grid_constant__ B
     S_.w.grp_cnt[r_] = 0;
     S_.w.kdraw[r_] = (r_ >= 1) ? fy_draw(rk, s, r_) : 0;
     const int len = stratum_of(t.P, S_.L, r_);
-    const int eff = source_walk(rk, G, s, b_s, deg_s, r_, len,
+    const int eff = source_walk(t.skey, G, s, b_s, deg_s, r_, len,
                                 S_.w.spos + (int64_t)r_ * Ls);
     S_.w.seff[r_] = eff;
     atomicAdd(small_view(S_.w.small).ctr + 1, (unsigned long long)eff);
@@ -259,9 +260,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
                 int32_t row_words) {
   extern __shared__ int32_t rows[];
   __shared__ PairSet ctx[kBlock / 32];
-  const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const uint32_t lanes_below = (1u << lane) - 1u;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   int32_t *my_cnt = rows + (2 * wib) * row_words;
   int32_t *my_R = my_cnt + row_words;
@@ -296,7 +295,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         S.pair_w = B.w.pair_w;
         S.Hc = B.w.Hc;
         S.n_pairs = sm.cnt[1];
-        S.s = (uint32_t)B.s;
+        S.key = B.tab->tkey;
       }
       __syncwarp();
     }
@@ -305,7 +304,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     unsigned long long W = 0;
     uint32_t deg_u = 0;
     const int32_t b_u = node_start(G, A.row_ptr, u, deg_u);
-    walk_target(rk, G, ctx[wib], (uint32_t)u, b_u, deg_u, lanes_below, c, W, st);
+    walk_target(G, ctx[wib], (uint32_t)u, b_u, deg_u, c, W, st);
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
       st += __shfl_xor_sync(0xffffffffu, st, off);
@@ -428,8 +427,9 @@ __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t 
 
 // a4+a5 of a batch with shared target walks: warps take targets (the nodes
 // with in-neighbours) from a counter; the 32 lanes walk the target's pairs
-// j = j0, j0 + 1, ... with lane refill, one Philox block (counter
-// ((i-1)>>1, j, u, kSharedWalkKey)) per odd and following even step; after
+// j = j0, j0 + 1, ... with lane refill, one Philox2x32-10 block (counter
+// (((i-1)>>1) << 24 | j, u) under the shared walk key) per odd and following
+// even step; after
 // every step the stepping lanes' nodes are tested against their pending
 // sources (shared_meet), and lane b writes source b's count, weight sum and
 // score at the end of the target.  A source's own row
@@ -446,7 +446,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     src[b] = ShSrc{B.wj, B.scores, B.counts, B.z, B.N_tot, B.s};
   }
   __syncthreads();
-  const RoundKeys rk = round_keys(A.key0, A.key1);
+  const uint32_t key = A.shared_key;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanes_below = (1u << lane) - 1u;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
@@ -497,14 +497,14 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         if (next >= J) break;
         continue;  // every pair of this round was dead: take the next ones
       }
-      uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+      uint32_t x0 = 0, x1 = 0;
       int32_t x = 0;
-      decltype(adj_entry(G, 0, 1, 0u, 0u)) e{};
+      decltype(adj_entry(G, 0, 0u)) e{};
       // odd step i
       bool stepped = live;
       if (stepped) {
-        philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)j, u, kSharedWalkKey, x0, x1, x2, x3);
-        e = adj_entry(G, b, deg, x0, x1);
+        philox2(key, walk_ctr0(i, (uint32_t)j), u, x0, x1);
+        e = step_entry(G, b, x0, deg, key, i, (uint32_t)j, u);
         x = entry_pos(G, e);
         ++st;
       }
@@ -526,7 +526,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
       // even step i + 1
       stepped = live;
       if (stepped) {
-        e = adj_entry(G, b, deg, x2, x3);
+        e = step_entry(G, b, x1, deg, key, i + 1, (uint32_t)j, u);
         x = entry_pos(G, e);
         ++st;
       }
@@ -884,6 +884,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     A.pos_bits = g->pos_bits;
     A.key0 = (uint32_t)seed;
     A.key1 = (uint32_t)(seed >> 32);
+    A.shared_key = walk_key(seed, kSharedWalkKey);
     A.M = d_M;
     A.H = d_H;
     A.Jmax = Jmax;

@@ -1,16 +1,20 @@
 // Device-side building blocks of the walk kernels (sm_103a).
 //
-// Philox4x32-10 is restated from its defining paper (Salmon, Moraes, Dror,
-// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds,
-// each multiplying counter words 0 and 2 by 0xD2511F53 and 0xCD9E8D57 into
-// 64-bit products, then
-//   x0' = hi(M1 x2) ^ x1 ^ k0,  x1' = lo(M1 x2),
-//   x2' = hi(M0 x0) ^ x3 ^ k1,  x3' = lo(M0 x0),
-// with the key advanced by the Weyl constants 0x9E3779B9 and 0xBB67AE85
-// after every round.  The key is launch-uniform, so the ten round keys are
-// computed once per thread.
+// Two generators of Salmon, Moraes, Dror, Shaw ("Parallel random numbers: as
+// easy as 1, 2, 3", SC'11) are restated from that paper's definitions:
+//   Philox4x32-10 (the Fisher-Yates draws): ten rounds, each multiplying
+//     counter words 0 and 2 by 0xD2511F53 and 0xCD9E8D57 into 64-bit
+//     products, then x0' = hi(M1 x2) ^ x1 ^ k0, x1' = lo(M1 x2),
+//     x2' = hi(M0 x0) ^ x3 ^ k1, x3' = lo(M0 x0), the key advanced by the
+//     Weyl constants 0x9E3779B9 and 0xBB67AE85 after every round;
+//   Philox2x32-10 (the walk steps): ten rounds of x0' = hi(M x0) ^ x1 ^ k,
+//     x1' = lo(M x0) with M = 0xD256D193, the 32-bit key advanced by
+//     0x9E3779B9 after every round.
+// Keys are launch- or warp-uniform, so the round keys are computed once.
 #pragma once
 #include <stdint.h>
+
+#include "srk_internal.h"
 
 namespace srk {
 
@@ -18,6 +22,7 @@ constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
 constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+constexpr uint32_t kPhilox2M = 0xD256D193u;
 
 struct RoundKeys {
   uint32_t k0[10];
@@ -50,6 +55,18 @@ __device__ __forceinline__ void philox(const RoundKeys &rk, uint32_t c0,
   }
 }
 
+// One Philox2x32-10 block: counter (c0, c1), key k -> 64 random bits (x0, x1).
+__device__ __forceinline__ void philox2(uint32_t k, uint32_t c0, uint32_t c1,
+                                        uint32_t &x0, uint32_t &x1) {
+  x0 = c0; x1 = c1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi = __umulhi(kPhilox2M, x0), lo = kPhilox2M * x0;
+    x0 = hi ^ x1 ^ (k + (uint32_t)r * kPhiloxW0);
+    x1 = lo;
+  }
+}
+
 // floor(R * d / 2^64) for a 64-bit draw R = (hi:lo) and 0 < d < 2^32: a
 // uniform index in [0, d).  R*d = hi*d*2^32 + lo*d, and adding the fraction
 // of lo*d/2^32 cannot carry past a multiple of 2^32, so
@@ -58,6 +75,40 @@ __device__ __forceinline__ uint32_t draw_index(uint32_t hi, uint32_t lo,
                                                uint32_t d) {
   const uint64_t t = (uint64_t)hi * d + __umulhi(lo, d);
   return (uint32_t)(t >> 32);
+}
+
+// Walk steps.  Step i of walk replica r from node v, under the query's walk
+// key k (walk_key): block ((i-1)>>1) << 24 | r, v) of Philox2x32-10 serves
+// the odd step i = 2t+1 (word x0) and the even step 2t+2 (word x1)
+// (r < 2^24, t < 2^7, v < 2^31: the top bits of both counter words stay
+// clear).  The in-neighbour index below d is Lemire's bounded draw ("Fast
+// random integer generation in an interval", ACM TOMACS 2019) of the 32-bit
+// word w: floor(w d / 2^32), accepted when (w d mod 2^32) >= 2^32 mod d, which
+// leaves exactly floor(2^32 / d) words per index; a rejected word (probability
+// below d / 2^32) is replaced by the 64-bit draw floor(R d / 2^64) from the
+// block whose counter has the top bit of word 0 (odd step) or word 1 (even
+// step) set, R = (x0:x1).  The index is uniform up to d / 2^64.
+__device__ __forceinline__ uint32_t walk_ctr0(int i, uint32_t r) {
+  return ((uint32_t)(i - 1) << 23 & 0x7F000000u) | r;
+}
+
+// The index of a step whose word was rejected (kept out of line: it runs on
+// fewer than d / 2^32 of the steps).
+static __device__ __noinline__ uint32_t step_index_redraw(uint32_t k, int i, uint32_t r,
+                                                          uint32_t v, uint32_t d) {
+  const uint32_t even = (uint32_t)(i - 1) & 1u;
+  uint32_t y0, y1;
+  philox2(k, walk_ctr0(i, r) | (even ? 0u : 0x80000000u), v | (even ? 0x80000000u : 0u),
+          y0, y1);
+  return draw_index(y0, y1, d);
+}
+
+// The lane's position among the warp's lanes below it (a mask), read from the
+// special register rather than kept live across the walk loop.
+__device__ __forceinline__ uint32_t lanes_below_mask() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
 }
 
 // Stratum (walk length) of walk index r: the l with P[l] <= r < P[l+1],
@@ -109,8 +160,8 @@ __host__ __device__ __forceinline__ Small small_view(int32_t *base) {
 
 // The walks hold the node they are at as (base, deg): the index of its
 // list's first entry and its in-degree.  Each layout supplies
-//   adj_entry(G, base, deg, hi, lo): the entry a step reads with the 64-bit
-//       draw (hi, lo), the in-neighbour of index floor(R deg / 2^64);
+//   adj_entry(G, base, k): entry k of the list, the in-neighbour a step
+//       reads with the index k drawn below deg (step_entry);
 //   entry_pos(G, e): the identity of the node that entry names (what the hit
 //       table holds);
 //   entry_next(G, e, x, deg): base (returned) and degree of that node x;
@@ -138,9 +189,8 @@ __host__ __device__ __forceinline__ Adj make_adj(const uint32_t *adj, const int3
   return a;
 }
 
-__device__ __forceinline__ uint32_t adj_entry(const Adj &G, int32_t base, uint32_t deg,
-                                              uint32_t hi, uint32_t lo) {
-  return G.adj[base + (int32_t)draw_index(hi, lo, deg)];
+__device__ __forceinline__ uint32_t adj_entry(const Adj &G, int32_t base, uint32_t k) {
+  return G.adj[base + (int32_t)k];
 }
 __device__ __forceinline__ int32_t entry_pos(const Adj &G, uint32_t e) {
   return (int32_t)(e & G.pmask);
@@ -179,9 +229,8 @@ __host__ __device__ __forceinline__ AdjW make_adjw(const uint32_t *words) {
   a.adj = reinterpret_cast<const uint2 *>(words);
   return a;
 }
-__device__ __forceinline__ uint2 adj_entry(const AdjW &G, int32_t base, uint32_t deg,
-                                           uint32_t hi, uint32_t lo) {
-  return G.adj[base + (int32_t)draw_index(hi, lo, deg)];
+__device__ __forceinline__ uint2 adj_entry(const AdjW &G, int32_t base, uint32_t k) {
+  return G.adj[base + (int32_t)k];
 }
 __device__ __forceinline__ int32_t entry_pos(const AdjW &, uint2 e) { return (int32_t)e.x; }
 __device__ __forceinline__ int32_t entry_next(const AdjW &, uint2 e, int32_t x,
@@ -202,9 +251,8 @@ struct AdjC {
   const int32_t *row_ptr;
   const int32_t *col;
 };
-__device__ __forceinline__ int32_t adj_entry(const AdjC &G, int32_t base, uint32_t deg,
-                                             uint32_t hi, uint32_t lo) {
-  return G.col[base + (int32_t)draw_index(hi, lo, deg)];
+__device__ __forceinline__ int32_t adj_entry(const AdjC &G, int32_t base, uint32_t k) {
+  return G.col[base + (int32_t)k];
 }
 __device__ __forceinline__ int32_t entry_pos(const AdjC &, int32_t e) { return e; }
 __device__ __forceinline__ int32_t entry_next(const AdjC &G, int32_t, int32_t x,
@@ -232,20 +280,36 @@ __device__ __forceinline__ auto adj_view(const uint32_t *words, const int32_t *p
   else return make_adj(words, pos, pb);
 }
 
-// Source walk r of length len from s (list base b_s, degree deg_s): writes
-// the identity of the node at step i to out[i-1]; returns the steps taken.
-// Step i draws from Philox counter ((i-1)>>1, r, s, s), words 2((i-1)&1), +1.
+// The entry step i of walk replica r from node v reads (list base b, degree
+// d), from the step's word w of block (walk_ctr0(i, r), v) under key k.  The
+// load of floor(w d / 2^32) is issued before the acceptance test, which only
+// replaces it when the word was rejected, so the test is off the chain of
+// dependent loads.
 template <class GA>
-__device__ __forceinline__ int source_walk(const RoundKeys &rk, const GA &G,
+__device__ __forceinline__ auto step_entry(const GA &G, int32_t b, uint32_t w, uint32_t d,
+                                           uint32_t k, int i, uint32_t r, uint32_t v) {
+  auto e = adj_entry(G, b, __umulhi(w, d));
+  const uint32_t lo = w * d;
+  if (lo < d && lo < (0u - d) % d) e = adj_entry(G, b, step_index_redraw(k, i, r, v, d));
+  return e;
+}
+
+// Source walk r of length len from s (list base b_s, degree deg_s) under the
+// source's walk key k: writes the identity of the node at step i to out[i-1];
+// returns the steps taken.
+template <class GA>
+__device__ __forceinline__ int source_walk(uint32_t k, const GA &G,
                                            uint32_t s, int32_t b_s, uint32_t deg_s,
                                            int32_t r, int len, int32_t *out) {
   int32_t b = b_s;
   uint32_t deg = deg_s;
-  uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+  uint32_t x0 = 0, x1 = 0;
   for (int i = 1; i <= len; ++i) {
     if (deg == 0) return i - 1;
-    if (i & 1) philox(rk, (uint32_t)(i - 1) >> 1, (uint32_t)r, s, s, x0, x1, x2, x3);
-    const auto e = adj_entry(G, b, deg, (i & 1) ? x0 : x2, (i & 1) ? x1 : x3);
+    if (i & 1) {
+      philox2(k, walk_ctr0(i, (uint32_t)r), s, x0, x1);
+    }
+    const auto e = step_entry(G, b, (i & 1) ? x0 : x1, deg, k, i, (uint32_t)r, s);
     const int32_t x = entry_pos(G, e);
     out[i - 1] = x;
     b = entry_next(G, e, x, deg);
@@ -290,17 +354,16 @@ struct PairSet {
   const unsigned long long *pair_w;
   const int32_t *Hc;
   int32_t n_pairs;     // cnt[1]
-  uint32_t s;          // source id (Philox counter word 3)
+  uint32_t key;        // walk key of the target walks (walk_key)
 };
 
 // All pairs of target u (list base b_u, degree deg_u > 0) walked by one
 // warp with lane refill; per-lane totals of meetings c, weight W and steps st
 // are added to the arguments (not reduced across the warp).
 template <class GA>
-__device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
+__device__ __forceinline__ void walk_target(const GA &G,
                                             const PairSet &S, uint32_t u,
-                                            int32_t b_u, uint32_t deg_u,
-                                            uint32_t lanes_below, uint32_t &c,
+                                            int32_t b_u, uint32_t deg_u, uint32_t &c,
                                             unsigned long long &W, uint32_t &st) {
   int32_t next = 0;  // first unassigned pair (warp-uniform)
   bool live = false;
@@ -310,7 +373,7 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
     const uint32_t idle = __ballot_sync(0xffffffffu, !live);
     if (idle) {
       if (!live) {
-        a = next + __popc(idle & lanes_below);
+        a = next + __popc(idle & lanes_below_mask());
         if (a < S.n_pairs) {
           live = true;
           j = (uint32_t)S.pair_j[a];
@@ -323,10 +386,10 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
     }
     if (!__any_sync(0xffffffffu, live)) break;
     if (live) {
-      uint32_t x0, x1, x2, x3;
-      philox(rk, (uint32_t)(i - 1) >> 1, j, u, S.s, x0, x1, x2, x3);
+      uint32_t x0, x1;
+      philox2(S.key, walk_ctr0(i, j), u, x0, x1);
       // odd step i
-      auto e = adj_entry(G, b, deg, x0, x1);
+      auto e = step_entry(G, b, x0, deg, S.key, i, j, u);
       int32_t x = entry_pos(G, e);
       ++st;
       if (x == S.Hc[S.R[i] + a]) {
@@ -341,7 +404,7 @@ __device__ __forceinline__ void walk_target(const RoundKeys &rk, const GA &G,
           live = false;  // no in-neighbours: the walk ends
         } else {
           // even step i+1
-          e = adj_entry(G, b, deg, x2, x3);
+          e = step_entry(G, b, x1, deg, S.key, i + 1, j, u);
           x = entry_pos(G, e);
           ++st;
           if (x == S.Hc[S.R[i + 1] + a]) {
@@ -378,15 +441,6 @@ namespace srk {
 // K_r(u) = low half of mix64(k_r ^ u) and k_r = mix64(seed + (4 s + r + 1)
 // 0x9E3779B97F4A7C15), mix64 the output function of SplitMix64 (Steele, Lea,
 // Flood, OOPSLA 2014).
-__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z ^= z >> 30;
-  z *= 0xBF58476D1CE4E5B9ull;
-  z ^= z >> 27;
-  z *= 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return z;
-}
-
 struct FeistelShape {
   int lo_bits, hi_bits;  // widths of B and A at the start
   int32_t N;
@@ -404,15 +458,6 @@ __host__ __device__ __forceinline__ FeistelShape feistel_shape(int32_t N, uint64
   for (int r = 0; r < 4; ++r)
     f.k[r] = mix64(seed + (4 * (uint64_t)s + (uint64_t)r + 1) * 0x9E3779B97F4A7C15ull);
   return f;
-}
-
-__device__ __forceinline__ uint32_t h32(uint32_t x) {
-  x ^= x >> 16;
-  x *= 0x7FEB352Du;
-  x ^= x >> 15;
-  x *= 0x846CA68Bu;
-  x ^= x >> 16;
-  return x;
 }
 
 // The round keys K_r(u) of target u.
@@ -452,12 +497,12 @@ __device__ __forceinline__ int32_t feistel_pi(const FeistelShape &f, const Feist
 
 // walk_target in the literal mode: pair a (index j, source length l1 stored
 // in pair_w[a]) walks target walk t = pi_u(j) of length l2 = stratum(t),
-// Philox replica t; it ends after min(l2, source cap) steps; a meeting adds
+// walk replica t; it ends after min(l2, source cap) steps; a meeting adds
 // round(a(l1) a(l2) 2^32).  P (stratum prefix, shared memory) and a (Lemma 7
 // weights) come from the query table.
 template <class GA>
 __device__ __forceinline__ void walk_target_literal(
-    const RoundKeys &rk, const GA &G, const PairSet &S, const FeistelShape &f,
+    const GA &G, const PairSet &S, const FeistelShape &f,
     const int32_t *P, int L, const double *aw, uint32_t u,
     int32_t b_u, uint32_t deg_u, uint32_t lanes_below, uint32_t &c,
     unsigned long long &W, uint32_t &st) {
@@ -505,9 +550,9 @@ __device__ __forceinline__ void walk_target_literal(
     }
     if (!__any_sync(0xffffffffu, live)) break;
     if (live) {
-      uint32_t x0, x1, x2, x3;
-      philox(rk, (uint32_t)(i - 1) >> 1, t, u, S.s, x0, x1, x2, x3);
-      auto e = adj_entry(G, b, deg, x0, x1);
+      uint32_t x0, x1;
+      philox2(S.key, walk_ctr0(i, t), u, x0, x1);
+      auto e = step_entry(G, b, x0, deg, S.key, i, t, u);
       int32_t x = entry_pos(G, e);
       ++st;
       if (x == S.Hc[S.R[i] + a]) {
@@ -521,7 +566,7 @@ __device__ __forceinline__ void walk_target_literal(
         if (deg == 0) {
           live = false;
         } else {
-          e = adj_entry(G, b, deg, x2, x3);
+          e = step_entry(G, b, x1, deg, S.key, i + 1, t, u);
           x = entry_pos(G, e);
           ++st;
           if (x == S.Hc[S.R[i + 1] + a]) {

@@ -143,6 +143,8 @@ int build_table(int32_t n, int32_t s, double c, double eps, uint64_t seed,
   t->key1 = (uint32_t)(seed >> 32);
   t->literal = (opt && (opt->flags & SRK_OPT_LITERAL_SHUFFLE)) ? 1 : 0;
   t->shared = (opt && (opt->flags & SRK_OPT_SHARED_WALKS)) ? 1 : 0;
+  t->skey = walk_key(seed, (uint32_t)s);
+  t->tkey = t->shared ? walk_key(seed, kSharedWalkKey) : t->skey;
   t->z = z;
   int64_t acc = 0;
   t->P[0] = 0;

@@ -54,11 +54,43 @@ struct srk_graph {
 
 namespace srk {
 
+// The output function of SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) and
+// the 32-bit finalizer "lowbias32" (C. Wellons, 2018); both are bijections.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+__host__ __device__ __forceinline__ uint32_t h32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// Key word of the shared target walks (SRK_OPT_SHARED_WALKS) in place of a
+// source (sources are below 2^31, so it names none).
+constexpr uint32_t kSharedWalkKey = 0xFFFFFFFEu;
+
+// The 32-bit Philox2x32-10 key of a query's walks: h32(q ^ low half of
+// mix64(seed)), q the source (its source walks, and its target walks by
+// default) or kSharedWalkKey (the shared target walks).  Injective in q for a
+// given seed, since h32 is a bijection.
+__host__ __device__ __forceinline__ uint32_t walk_key(uint64_t seed, uint32_t q) {
+  return h32(q ^ (uint32_t)mix64(seed));
+}
+
 // Sample-count table of one query (Algorithm 1 lines 3-5, Algorithm 2 line 2,
 // Lemma 7).  Passed by value as a kernel parameter (stays below 4 KB).
 struct QueryTab {
   int32_t s, n, L, N_tot;
-  uint32_t key0, key1;
+  uint32_t key0, key1;  // the seed's halves (Fisher-Yates draws, literal shuffle)
+  uint32_t skey, tkey;  // walk keys of the source walks and of the target walks
   int32_t literal;  // 1: literal target shuffle (SRK_OPT_LITERAL_SHUFFLE)
   int32_t shared;   // 1: shared target walks (SRK_OPT_SHARED_WALKS)
   double z;
@@ -130,9 +162,6 @@ int target_range(const srk_graph *g, const srk_opts *opt, int32_t *b, int32_t *e
 __global__ void k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off,
                        int32_t N);
 
-// Philox counter word 3 of the target walks: the source, or this constant
-// with SRK_OPT_SHARED_WALKS (sources are below 2^31, so it names none).
-constexpr uint32_t kSharedWalkKey = 0xFFFFFFFEu;
 
 // Releases the graph's linear topology, if built (srk_linear.cu).
 void free_lin_topo(srk_graph *g);

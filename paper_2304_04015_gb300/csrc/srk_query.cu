@@ -25,10 +25,10 @@
 namespace srk {
 
 // ---------------------------------------------------------------- step a2 --
-// Walk r of the source has length l = stratum(r).  Step i >= 1 draws 64 bits
-// from Philox counter ((i-1)>>1, r, s, s), word pair 2*((i-1)&1) (high, low),
-// and moves to I(x)[floor(R * |I(x)| / 2^64)]; it stops early at a node with
-// no in-neighbours.  Walks run on the graph's adjacency layout (a packed copy
+// Walk r of the source has length l = stratum(r).  Step i >= 1 moves to
+// I(x)[k], k the bounded draw below |I(x)| from word (i-1)&1 of the
+// Philox2x32-10 block (((i-1)>>1) << 24 | r, s) under the source's walk key
+// (step_entry); it stops early at a node with no in-neighbours.  Walks run on the graph's adjacency layout (a packed copy
 // in which nodes are identified by their position, or the CSR itself).  The
 // same thread computes Fisher-Yates draw t = r, k_t = floor(R * (t+1) / 2^64)
 // with R from counter (t>>1, ~0, ~0, s).
@@ -55,7 +55,7 @@ k_source_walks(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ 
     grp_cnt[r] = 0;
     kdraw[r] = (r >= 1) ? fy_draw(rk, s, r) : 0;
     const int len = stratum_of(P, tab.L, r);
-    const int eff = source_walk(rk, G, s, b_s, deg_s, r, len, spos + (int64_t)r * Ls);
+    const int eff = source_walk(tab.skey, G, s, b_s, deg_s, r, len, spos + (int64_t)r * Ls);
     seff[r] = eff;
     steps += (unsigned long long)eff;
   }
@@ -263,9 +263,10 @@ k_hit_table(const __grid_constant__ QueryTab tab, const int32_t *__restrict__ si
 // the packed adjacency: from a node at position p with degree d, a step reads
 // entry adj[p + 1 + index], which holds the next node's position and, unless
 // that node's degree is large, its degree as well.  Pair a (original index
-// j) walks from u: one Philox block, counter ((i-1)>>1, j, u, s), serves the
-// odd step i (words 0,1) and the even step i+1 (words 2,3).  A step moves to
-// I(x)[floor(R |I(x)| / 2^64)]; the walk meets when its node equals row i of
+// j) walks from u: one Philox2x32-10 block, counter (((i-1)>>1) << 24 | j, u)
+// under the target walks' key, serves the odd step i (word 0) and the even
+// step i+1 (word 1).  A step moves to I(x)[k], k the bounded draw below |I(x)|
+// (step_entry); the walk meets when its node equals row i of
 // the hit table, ends after cap steps (a >= cnt[i+1]) or at a node without
 // in-neighbours.  The first meeting adds 1 to the count and the pair's weight
 // to W_u.  The warp then reduces and writes count, W and s~(s,u) = W 2^-32 / z
@@ -277,7 +278,7 @@ struct TargetArgs {
   const int32_t *npos;     // 4-byte-entry layout: node positions
   int32_t pos_bits;
   int32_t n, s, L;
-  uint32_t walk_key;       // Philox counter word 3 of the target walks (s or shared)
+  uint32_t walk_key;       // walk key of the target walks (the source's or the shared one)
   uint32_t key0, key1;
   double z;
   const int32_t *small_base;
@@ -319,7 +320,6 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
     }
   }
   __syncthreads();
-  const RoundKeys rk = round_keys(A.key0, A.key1);
   const int lane = threadIdx.x & 31;
   const uint32_t lanes_below = (1u << lane) - 1u;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
@@ -330,7 +330,7 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   S.pair_w = A.pair_w;
   S.Hc = A.Hc;
   S.n_pairs = cnt[1];
-  S.s = A.walk_key;
+  S.key = A.walk_key;
   FeistelShape fs;
   if constexpr (kLiteral)
     fs = feistel_shape(A.N_tot, ((uint64_t)A.key1 << 32) | A.key0, (uint32_t)A.s);
@@ -355,10 +355,10 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
     const int32_t b_u = node_start(G, A.row_ptr, u, deg_u);
     if (u != A.s && deg_u > 0) {
       if (kLiteral)
-        walk_target_literal(rk, G, S, fs, Psh, A.L, X.a, (uint32_t)u, b_u, deg_u,
+        walk_target_literal(G, S, fs, Psh, A.L, X.a, (uint32_t)u, b_u, deg_u,
                             lanes_below, c, W, st);
       else
-        walk_target(rk, G, S, (uint32_t)u, b_u, deg_u, lanes_below, c, W, st);
+        walk_target(G, S, (uint32_t)u, b_u, deg_u, c, W, st);
     }
     for (int off = 16; off > 0; off >>= 1) {
       c += __shfl_xor_sync(0xffffffffu, c, off);
@@ -477,7 +477,7 @@ int enqueue_query(const srk_graph *g, const QueryTab &t, const Workspace &w,
   A.pos_bits = g->pos_bits;
   A.n = g->n;
   A.s = t.s;
-  A.walk_key = t.shared ? kSharedWalkKey : (uint32_t)t.s;
+  A.walk_key = t.tkey;
   A.L = t.L;
   A.key0 = t.key0;
   A.key1 = t.key1;

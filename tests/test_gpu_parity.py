@@ -556,6 +556,52 @@ def test_hub_headers_bit_exact(srk):
         assert np.array_equal(rows[layout][1], rows["narrow"][1])
 
 
+def test_rejected_step_words_redraw_bit_exact(srk):
+    # Two hubs whose in-lists hold all D = 3,144,261 leaves, each leaf with
+    # both hubs as in-neighbours: every even step of a walk from a leaf draws
+    # an index below D, and 2^32 mod D = 3,051,031, so 7.1e-4 of those words
+    # are rejected and replaced by the 64-bit draw of the step's second
+    # block (source and target walks, per-source and shared keys).
+    import torch
+    from oracle import sampler
+    from srk_inputs import csr_from_edges
+    D = 3144261
+    leaves = np.arange(2, D + 2, dtype=np.int32)
+    src = np.concatenate([leaves, leaves, np.zeros(D, np.int32), np.ones(D, np.int32)])
+    dst = np.concatenate([np.zeros(D, np.int32), np.ones(D, np.int32), leaves, leaves])
+    rp, col = csr_from_edges(D + 2, src, dst)
+    n = rp.size - 1
+    assert np.diff(rp)[0] == D and (1 << 32) % D == 3051031
+    s, seed = 77, 31
+    kw = dict(z_override=2000.0, L_override=16)
+    rng = np.random.default_rng(4)
+    targets = np.unique(np.concatenate([[0, 1, s], rng.choice(n, 120, replace=False)]))
+    targets = targets.astype(np.int32)
+    # words of step 2 (the first hub draw of a pair) that the rule rejects
+    key = sampler.walk_key(seed, s)
+    t_ = (1 << 32) % D
+    rejected = sum(1 for u in targets[2:40] for j in range(2000)
+                   if (sampler.philox2x32_10([j, int(u)], key)[1] * D) % (1 << 32) < t_)
+    assert rejected >= 20
+    dev = torch.device("cuda:0")
+    for shared in (False, True):
+        gpu = gpu_query(srk, rp, col, s, 0.1, seed, shared_walks=shared, **kw)
+        ref = oracle_query(rp, col, s, 0.1, seed, targets=targets, shared_walks=shared, **kw)
+        assert_parity(gpu, ref, targets)
+        assert ref.count.sum() > 0
+    g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                           layout="wide")
+    try:
+        cnt = torch.empty(n, dtype=torch.int32, device=dev)
+        srk.srk_single_source(g, s, C, 0.1, seed, torch.empty(n, dtype=torch.float64,
+                                                               device=dev), cnt, **kw)
+        torch.cuda.synchronize()
+        ref = oracle_query(rp, col, s, 0.1, seed, targets=targets, **kw)
+        assert np.array_equal(cnt.cpu().numpy().view(np.uint32)[targets], ref.count)
+    finally:
+        g.close()
+
+
 def test_multi_source_long_walks_shared_memory(srk):
     # L = 250: in its 1024-thread launch shape the batched kernel's per-warp
     # rows take ~65 KB of shared memory, above the 48 KB a kernel gets without
