@@ -52,7 +52,7 @@ struct BatchArgs {
   uint32_t key0, key1;
   uint32_t shared_key;  // walk key of the shared target walks
   uint4 *M;       // shared walks: M[(i-1) Jmax + j].x bit b = pair j of batch source
-                  // b may still meet at step i (cap_b(j) >= i); (.y, .z) = the
+                  // b may still meet at step i (cap_b(j) >= i); (.z, .w) = the
                   // 64-bit signature of those sources' nodes at step i (bit
                   // node_hash(node) per node); Lmax + 1 rows
   int32_t *H;     // shared walks: H[((i-1) Jmax + j) k + b] = node of source b's walk
@@ -337,10 +337,10 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
 __device__ __forceinline__ uint32_t node_hash(int32_t x) {
   return ((uint32_t)x * 0x9E3779B9u) >> 26;
 }
-// Is the bit of node x set in the signature (lo, hi)?
-__device__ __forceinline__ bool sig_has(uint32_t lo, uint32_t hi, int32_t x) {
+// Is the bit of node x set in the signature (sig.x: bits 0-31, sig.y: 32-63)?
+__device__ __forceinline__ bool sig_has(uint2 sig, int32_t x) {
   const uint32_t h = node_hash(x);
-  return ((h < 32 ? lo : hi) >> (h & 31)) & 1u;
+  return ((h < 32 ? sig.x : sig.y) >> (h & 31)) & 1u;
 }
 
 // Per source and pair j: the pair's weight, its hit-table column (steps
@@ -362,7 +362,7 @@ __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
       uint4 *cell = &A.M[(int64_t)(q - 1) * A.Jmax + j];
       const uint32_t h = node_hash(sp[q - 1]);
       atomicOr(&cell->x, bit);
-      atomicOr(h < 32 ? &cell->y : &cell->z, 1u << (h & 31));
+      atomicOr(h < 32 ? &cell->z : &cell->w, 1u << (h & 31));
     }
   })
 }
@@ -384,19 +384,18 @@ struct ShSrc {
 // l (node x_l, pair j_l, record offset r_l, pending sources p_l) lane b
 // compares the node of source b's walk, H[r_l + b], with x_l, so one
 // coalesced line serves all of lane l's sources, and lane b counts source
-// b's meetings in registers (c_b, w_b).  A lane whose node's bit is clear in
-// the step's signature (sig_lo, sig_hi) skips the test.  Returns the sources that met on
+// b's meetings in its own words cnt[b], wsum[b] (no atomics).  A lane whose node's bit is clear in
+// the step's signature sig skips the test.  Returns the sources that met on
 // this lane's own pair.
 template <bool kCoop>
 __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t *H, int k,
                                                 bool stepped, int32_t x, uint32_t rec,
-                                                uint32_t pend, uint32_t sig_lo, uint32_t sig_hi,
+                                                uint32_t pend, uint2 sig,
                                                 int32_t j, int lane,
-                                                uint32_t *cnt, unsigned long long *wsum,
-                                                uint32_t &c_b, unsigned long long &w_b) {
+                                                uint32_t *cnt, unsigned long long *wsum) {
   uint32_t mine = 0u;
   if constexpr (!kCoop) {
-    if (stepped && sig_has(sig_lo, sig_hi, x))
+    if (stepped && sig_has(sig, x))
       for (uint32_t m = pend; m; m &= m - 1) {
         const int b = __ffs(m) - 1;
         if (H[rec + (uint32_t)b] == x) {
@@ -406,7 +405,7 @@ __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t 
         }
       }
   } else {
-    const bool maybe = stepped && pend != 0u && sig_has(sig_lo, sig_hi, x);
+    const bool maybe = stepped && pend != 0u && sig_has(sig, x);
     for (uint32_t m = __ballot_sync(0xffffffffu, maybe); m; m &= m - 1) {
       const int l = __ffs(m) - 1;
       const int32_t xl = __shfl_sync(0xffffffffu, x, l);
@@ -417,8 +416,8 @@ __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t 
       const uint32_t met = __ballot_sync(0xffffffffu, hit);
       if (lane == l) mine = met;
       if (hit) {
-        ++c_b;
-        w_b += src[lane].wj[jl];
+        cnt[lane] += 1u;
+        wsum[lane] += src[lane].wj[jl];
       }
     }
   }
@@ -434,13 +433,23 @@ __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t 
 // sources (shared_meet), and lane b writes source b's count, weight sum and
 // score at the end of the target.  A source's own row
 // keeps its prefilled 1.
+// Blocks per SM: 8 (32 registers) where the kernel fits them without
+// spills, else 6.  At 8 the step signatures are read from the records when
+// tested, at 6 they are kept in registers from the mask row's load.
 template <int kLayout, bool kCoop>
-__global__ void __launch_bounds__(256, 6)
+constexpr int shared_walk_blocks() { return (kLayout == kNarrow && kCoop) ? 8 : 6; }
+
+template <int kLayout, bool kCoop>
+__global__ void __launch_bounds__(256, shared_walk_blocks<kLayout, kCoop>())
 kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
                 int32_t n_act, int32_t j0, unsigned long long *__restrict__ ctr) {
   __shared__ ShSrc src[32];
   __shared__ uint32_t cnt[8][32];
   __shared__ unsigned long long wsum[8][32];
+  // per warp: the sources whose own row the target is, and the target's list
+  // (read at refills only, so they hold no registers across the walk)
+  __shared__ uint32_t w_excl[8], w_deg[8];
+  __shared__ int32_t w_base[8];
   for (int b = threadIdx.x; b < A.k; b += blockDim.x) {
     const BatchSrc &B = A.src[b];
     src[b] = ShSrc{B.wj, B.scores, B.counts, B.z, B.N_tot, B.s};
@@ -448,7 +457,6 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   __syncthreads();
   const uint32_t key = A.shared_key;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const uint32_t lanes_below = (1u << lane) - 1u;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   const uint4 *M = A.M;
   const int32_t J = A.Jmax;
@@ -462,33 +470,54 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     const uint32_t u = (uint32_t)act[q];
     // sources whose own row this target is
     const uint32_t excl = __ballot_sync(0xffffffffu, lane < k && src[lane].s == (int32_t)u);
-    uint32_t c_b = 0;                // kCoop, lane b: meetings of source b at this target
-    unsigned long long w_b = 0;      // kCoop, lane b: their weight sum
-    if constexpr (!kCoop) {
-      cnt[wib][lane] = 0u;
-      wsum[wib][lane] = 0ull;
-      __syncwarp();
+    cnt[wib][lane] = 0u;            // meetings of source `lane` at this target
+    wsum[wib][lane] = 0ull;         // and their weight sum
+    if (lane == 0) {
+      uint32_t deg_u = 0;
+      w_base[wib] = node_start(G, A.row_ptr, (int32_t)u, deg_u);
+      w_deg[wib] = deg_u;
+      w_excl[wib] = excl;
     }
-    uint32_t deg_u = 0;
-    const int32_t b_u = node_start(G, A.row_ptr, (int32_t)u, deg_u);
+    __syncwarp();
     uint32_t st = 0;
     int32_t next = j0, j = 0, i = 1, b = 0;
     bool live = false;
-    uint32_t deg = 0, pend = 0, sig_lo = 0, sig_hi = 0;
+    uint32_t deg = 0, pend = 0;
+    uint2 sg = make_uint2(0u, 0u);  // at 6 blocks per SM: the signature of the next test
+    constexpr bool kSigLoad = shared_walk_blocks<kLayout, kCoop>() == 8;
+    auto sig_of = [&](int64_t row, bool stepped_) -> uint2 {
+      if constexpr (kSigLoad)
+        return stepped_ ? *reinterpret_cast<const uint2 *>(&M[row].z) : make_uint2(0u, 0u);
+      else
+        return sg;
+    };
+    // pend &= the mask of row `row` (and, at 6 blocks per SM, its signature)
+    auto next_mask = [&](int64_t row) {
+      if constexpr (kSigLoad) {
+        pend &= M[row].x;
+      } else {
+        const uint4 mn = M[row];
+        pend &= mn.x;
+        sg = make_uint2(mn.z, mn.w);
+      }
+    };
     for (;;) {
       const uint32_t idle = __ballot_sync(0xffffffffu, !live);
       if (idle) {
         if (!live) {
-          j = next + __popc(idle & lanes_below);
+          j = next + __popc(idle & lanes_below_mask());
           if (j < J) {
-            const uint4 m1 = M[j];
-            pend = m1.x & ~excl;
-            sig_lo = m1.y;
-            sig_hi = m1.z;
+            if constexpr (kSigLoad) {
+              pend = M[j].x & ~w_excl[wib];
+            } else {
+              const uint4 m1 = M[j];
+              pend = m1.x & ~w_excl[wib];
+              sg = make_uint2(m1.z, m1.w);
+            }
             live = pend != 0u;
             i = 1;
-            b = b_u;
-            deg = deg_u;
+            b = w_base[wib];
+            deg = w_deg[wib];
           }
         }
         next += __popc(idle);
@@ -509,13 +538,11 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         ++st;
       }
       pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
-                                  (uint32_t)(((int64_t)(i - 1) * J + j) * k), pend, sig_lo, sig_hi, j, lane,
-                                  cnt[wib], wsum[wib], c_b, w_b);
+                                  (uint32_t)(((int64_t)(i - 1) * J + j) * k), pend,
+                                  sig_of((int64_t)(i - 1) * J + j, stepped), j, lane,
+                                  cnt[wib], wsum[wib]);
       if (stepped) {
-        const uint4 mn = M[(int64_t)i * J + j];  // still able to meet at step i + 1
-        pend &= mn.x;
-        sig_lo = mn.y;
-        sig_hi = mn.z;
+        next_mask((int64_t)i * J + j);  // still able to meet at step i + 1
         if (!pend) {
           live = false;
         } else {
@@ -531,13 +558,11 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         ++st;
       }
       pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
-                                  (uint32_t)(((int64_t)i * J + j) * k), pend, sig_lo, sig_hi, j, lane,
-                                  cnt[wib], wsum[wib], c_b, w_b);
+                                  (uint32_t)(((int64_t)i * J + j) * k), pend,
+                                  sig_of((int64_t)i * J + j, stepped), j, lane,
+                                  cnt[wib], wsum[wib]);
       if (stepped) {
-        const uint4 mn = M[(int64_t)(i + 1) * J + j];
-        pend &= mn.x;
-        sig_lo = mn.y;
-        sig_hi = mn.z;
+        next_mask((int64_t)(i + 1) * J + j);
         if (!pend) {
           live = false;
         } else {
@@ -550,11 +575,11 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(0xffffffffu, st, off);
     warp_steps += st;
     __syncwarp();
-    if (lane < k && !((excl >> lane) & 1u)) {
+    if (lane < k && !((w_excl[wib] >> lane) & 1u)) {
       const ShSrc &S = src[lane];
-      const unsigned long long W = kCoop ? w_b : wsum[wib][lane];
+      const unsigned long long W = wsum[wib][lane];
       S.scores[u] = (double)W * 2.3283064365386963e-10 / S.z;
-      if (S.counts) S.counts[u] = kCoop ? c_b : cnt[wib][lane];
+      if (S.counts) S.counts[u] = cnt[wib][lane];
     }
     __syncwarp();
   }
