@@ -55,9 +55,16 @@ struct BatchArgs {
                   // b may still meet at step i (cap_b(j) >= i); (.z, .w) = the
                   // 64-bit signature of those sources' nodes at step i (bit
                   // node_hash(node) per node); Lmax + 1 rows
-  int32_t *H;     // shared walks: H[((i-1) Jmax + j) k + b] = node of source b's walk
-                  // sigma_b(j) at step i, for i <= cap_b(j): one record per (step, pair)
+  uint2 *T;       // shared walks: the meeting tables, one per (step i, pair j) with
+                  // j >= Pmin_i (below, no pair of the batch reaches step i) at
+                  // T + ((rowbase[i] + j) << tbits): 2^tbits slots {node + 1,
+                  // the sources b with cap_b(j) >= i whose walk sigma_b(j) is at
+                  // that node at step i}, empty slots {0, 0}, linear probing from
+                  // slot_of(node)
+  const int64_t *rowbase;  // shared walks: rowbase[i] = tables before step i - Pmin_i
+  int32_t tbits;  // shared walks: log2 of the slots per table (>= 2 k)
   int32_t Jmax;   // shared walks: the largest N_tot of the batch
+  int32_t Lmax;   // shared walks: the largest L of the batch
 };
 
 __device__ __forceinline__ int find_source(const int64_t *off, int k, int64_t g) {
@@ -328,9 +335,9 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
 // source b the pair meets at the first step i <= cap_b(j) where the walk is
 // at the node of source b's walk sigma_b(j) at step i, exactly as
 // srk_single_source with the same flag decides it.  Those nodes of all the
-// batch's sources sit together in one record per (step, pair), so the test of
-// every pending source reads one line.  Batches hold at most 32 sources (one
-// mask bit each).
+// batch's sources sit in one small hash table per (step, pair), so a walk
+// tests every pending source with one lookup of its own node (one sector,
+// rarely two).  Batches hold at most 32 sources (one mask bit each).
 
 // One of 64 bits for a node: the signature of a (step, pair) record has the
 // bits of its nodes, so a walk whose node's bit is clear meets no source there.
@@ -342,10 +349,15 @@ __device__ __forceinline__ bool sig_has(uint2 sig, int32_t x) {
   const uint32_t h = node_hash(x);
   return ((h < 32 ? sig.x : sig.y) >> (h & 31)) & 1u;
 }
+// The first slot of node x in a meeting table of 2^tbits slots.
+__device__ __forceinline__ uint32_t slot_of(int32_t x, int tbits) {
+  return ((uint32_t)x * 0x85EBCA6Bu) >> (32 - tbits);
+}
 
-// Per source and pair j: the pair's weight, its hit-table column (steps
-// 1..cap(j) of source walk sigma(j)), its bit in the step masks and its
-// node's bit in the step signatures.
+// Per source and pair j: the pair's weight, its bit in the step masks, its
+// node's bit in the step signatures and its bit in the meeting tables of
+// steps 1..cap(j) (source walk sigma(j)).  A table holds at most k nodes in
+// 2^tbits >= 2k slots, so an insertion always finds its node or a free slot.
 __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
   SRK_BATCH_LOOP(A, {
     const int32_t j = r_;
@@ -357,12 +369,23 @@ __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
     const int Ls = S_.L > 0 ? S_.L : 1;
     const int32_t *sp = S_.w.spos + (int64_t)w * Ls;
     const uint32_t bit = 1u << i_;
+    const uint32_t smask = (1u << A.tbits) - 1u;
     for (int q = 1; q <= cap; ++q) {
-      A.H[((int64_t)(q - 1) * A.Jmax + j) * A.k + i_] = sp[q - 1];
+      const int32_t node = sp[q - 1];
       uint4 *cell = &A.M[(int64_t)(q - 1) * A.Jmax + j];
-      const uint32_t h = node_hash(sp[q - 1]);
+      const uint32_t h = node_hash(node);
       atomicOr(&cell->x, bit);
       atomicOr(h < 32 ? &cell->z : &cell->w, 1u << (h & 31));
+      uint2 *tab = A.T + ((A.rowbase[q] + j) << A.tbits);
+      const uint32_t key = (uint32_t)node + 1u;
+      uint32_t sl = slot_of(node, A.tbits);
+      for (uint32_t probe = 0; probe <= smask; ++probe, sl = (sl + 1u) & smask) {
+        const uint32_t prev = atomicCAS(&tab[sl].x, 0u, key);
+        if (prev == 0u || prev == key) {
+          atomicOr(&tab[sl].y, bit);
+          break;
+        }
+      }
     }
   })
 }
@@ -376,52 +399,34 @@ struct ShSrc {
   int32_t N, s;
 };
 
-// The meeting test after a step, in one of two forms.  kCoop = false: each
-// stepping lane checks its own pending sources, reading their entries of its
-// record, and counts meetings with shared-memory atomics (cnt, wsum, indexed
-// by source).  kCoop = true, for batches whose pairs are pending for many
-// sources at once: the whole warp checks together -- for every stepping lane
-// l (node x_l, pair j_l, record offset r_l, pending sources p_l) lane b
-// compares the node of source b's walk, H[r_l + b], with x_l, so one
-// coalesced line serves all of lane l's sources, and lane b counts source
-// b's meetings in its own words cnt[b], wsum[b] (no atomics).  A lane whose node's bit is clear in
-// the step's signature sig skips the test.  Returns the sources that met on
-// this lane's own pair.
-template <bool kCoop>
-__device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t *H, int k,
-                                                bool stepped, int32_t x, uint32_t rec,
-                                                uint32_t pend, uint2 sig,
-                                                int32_t j, int lane,
+// The meeting test after a step: a stepping lane whose node x has its bit
+// in the step's signature looks x up in the step's meeting table (tab); the
+// pending sources among the slot's are those that meet here.  Their counts
+// and weight sums go to the warp's shared words cnt[b], wsum[b] (atomics:
+// lanes of a warp can meet the same source at once).  Returns them.
+__device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const uint2 *tab, int tbits,
+                                                bool stepped, int32_t x, uint32_t pend,
+                                                uint2 sig, int32_t j,
                                                 uint32_t *cnt, unsigned long long *wsum) {
-  uint32_t mine = 0u;
-  if constexpr (!kCoop) {
-    if (stepped && sig_has(sig, x))
-      for (uint32_t m = pend; m; m &= m - 1) {
-        const int b = __ffs(m) - 1;
-        if (H[rec + (uint32_t)b] == x) {
-          atomicAdd(&cnt[b], 1u);
-          atomicAdd(&wsum[b], src[b].wj[j]);
-          mine |= 1u << b;
-        }
+  uint32_t hits = 0u;
+  if (stepped && pend != 0u && sig_has(sig, x)) {
+    const uint32_t smask = (1u << tbits) - 1u, key = (uint32_t)x + 1u;
+    uint32_t sl = slot_of(x, tbits);
+    for (uint32_t probe = 0; probe <= smask; ++probe, sl = (sl + 1u) & smask) {
+      const uint2 e = tab[sl];
+      if (e.x == key) {
+        hits = e.y & pend;
+        break;
       }
-  } else {
-    const bool maybe = stepped && pend != 0u && sig_has(sig, x);
-    for (uint32_t m = __ballot_sync(0xffffffffu, maybe); m; m &= m - 1) {
-      const int l = __ffs(m) - 1;
-      const int32_t xl = __shfl_sync(0xffffffffu, x, l);
-      const uint32_t rl = __shfl_sync(0xffffffffu, rec, l);
-      const uint32_t pl = __shfl_sync(0xffffffffu, pend, l);
-      const int32_t jl = __shfl_sync(0xffffffffu, j, l);
-      const bool hit = lane < k && ((pl >> lane) & 1u) && H[rl + (uint32_t)lane] == xl;
-      const uint32_t met = __ballot_sync(0xffffffffu, hit);
-      if (lane == l) mine = met;
-      if (hit) {
-        cnt[lane] += 1u;
-        wsum[lane] += src[lane].wj[jl];
-      }
+      if (e.x == 0u) break;
+    }
+    for (uint32_t m = hits; m; m &= m - 1) {
+      const int b = __ffs(m) - 1;
+      atomicAdd(&cnt[b], 1u);
+      atomicAdd(&wsum[b], src[b].wj[j]);
     }
   }
-  return mine;
+  return hits;
 }
 
 // a4+a5 of a batch with shared target walks: warps take targets (the nodes
@@ -433,14 +438,10 @@ __device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const int32_t 
 // sources (shared_meet), and lane b writes source b's count, weight sum and
 // score at the end of the target.  A source's own row
 // keeps its prefilled 1.
-// Blocks per SM: 8 (32 registers) where the kernel fits them without
-// spills, else 6.  At 8 the step signatures are read from the records when
-// tested, at 6 they are kept in registers from the mask row's load.
-template <int kLayout, bool kCoop>
-constexpr int shared_walk_blocks() { return (kLayout == kNarrow && kCoop) ? 8 : 6; }
-
-template <int kLayout, bool kCoop>
-__global__ void __launch_bounds__(256, shared_walk_blocks<kLayout, kCoop>())
+// 6 blocks of 256 threads per SM (40 registers): at 8 (32 registers) every
+// form spilled.
+template <int kLayout>
+__global__ void __launch_bounds__(256, 6)
 kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
                 int32_t n_act, int32_t j0, unsigned long long *__restrict__ ctr) {
   __shared__ ShSrc src[32];
@@ -450,6 +451,9 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   // (read at refills only, so they hold no registers across the walk)
   __shared__ uint32_t w_excl[8], w_deg[8];
   __shared__ int32_t w_base[8];
+  __shared__ long long rowbase[SRK_MAX_LEN + 2];  // meeting-table rows (A.rowbase)
+  for (int i = threadIdx.x; i <= SRK_MAX_LEN + 1; i += blockDim.x)
+    rowbase[i] = (i <= A.Lmax) ? A.rowbase[i] : 0;
   for (int b = threadIdx.x; b < A.k; b += blockDim.x) {
     const BatchSrc &B = A.src[b];
     src[b] = ShSrc{B.wj, B.scores, B.counts, B.z, B.N_tot, B.s};
@@ -460,7 +464,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   const uint4 *M = A.M;
   const int32_t J = A.Jmax;
-  const int k = A.k;
+  const int tbits = A.tbits;
   unsigned long long warp_steps = 0;
   for (;;) {
     int32_t q = 0;
@@ -469,7 +473,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     if (q >= n_act) break;
     const uint32_t u = (uint32_t)act[q];
     // sources whose own row this target is
-    const uint32_t excl = __ballot_sync(0xffffffffu, lane < k && src[lane].s == (int32_t)u);
+    const uint32_t excl = __ballot_sync(0xffffffffu, lane < A.k && src[lane].s == (int32_t)u);
     cnt[wib][lane] = 0u;            // meetings of source `lane` at this target
     wsum[wib][lane] = 0ull;         // and their weight sum
     if (lane == 0) {
@@ -483,23 +487,12 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     int32_t next = j0, j = 0, i = 1, b = 0;
     bool live = false;
     uint32_t deg = 0, pend = 0;
-    uint2 sg = make_uint2(0u, 0u);  // at 6 blocks per SM: the signature of the next test
-    constexpr bool kSigLoad = shared_walk_blocks<kLayout, kCoop>() == 8;
-    auto sig_of = [&](int64_t row, bool stepped_) -> uint2 {
-      if constexpr (kSigLoad)
-        return stepped_ ? *reinterpret_cast<const uint2 *>(&M[row].z) : make_uint2(0u, 0u);
-      else
-        return sg;
-    };
-    // pend &= the mask of row `row` (and, at 6 blocks per SM, its signature)
+    uint2 sg = make_uint2(0u, 0u);  // the signature of the next test
+    // pend &= the mask of row `row`; sg = its signature
     auto next_mask = [&](int64_t row) {
-      if constexpr (kSigLoad) {
-        pend &= M[row].x;
-      } else {
-        const uint4 mn = M[row];
-        pend &= mn.x;
-        sg = make_uint2(mn.z, mn.w);
-      }
+      const uint4 mn = M[row];
+      pend &= mn.x;
+      sg = make_uint2(mn.z, mn.w);
     };
     for (;;) {
       const uint32_t idle = __ballot_sync(0xffffffffu, !live);
@@ -507,13 +500,9 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         if (!live) {
           j = next + __popc(idle & lanes_below_mask());
           if (j < J) {
-            if constexpr (kSigLoad) {
-              pend = M[j].x & ~w_excl[wib];
-            } else {
-              const uint4 m1 = M[j];
-              pend = m1.x & ~w_excl[wib];
-              sg = make_uint2(m1.z, m1.w);
-            }
+            const uint4 m1 = M[j];
+            pend = m1.x & ~w_excl[wib];
+            sg = make_uint2(m1.z, m1.w);
             live = pend != 0u;
             i = 1;
             b = w_base[wib];
@@ -537,10 +526,8 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         x = entry_pos(G, e);
         ++st;
       }
-      pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
-                                  (uint32_t)(((int64_t)(i - 1) * J + j) * k), pend,
-                                  sig_of((int64_t)(i - 1) * J + j, stepped), j, lane,
-                                  cnt[wib], wsum[wib]);
+      pend &= ~shared_meet(src, A.T + ((rowbase[i] + j) << tbits), tbits, stepped, x, pend,
+                           sg, j, cnt[wib], wsum[wib]);
       if (stepped) {
         next_mask((int64_t)i * J + j);  // still able to meet at step i + 1
         if (!pend) {
@@ -557,10 +544,8 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
         x = entry_pos(G, e);
         ++st;
       }
-      pend &= ~shared_meet<kCoop>(src, A.H, k, stepped, x,
-                                  (uint32_t)(((int64_t)i * J + j) * k), pend,
-                                  sig_of((int64_t)i * J + j, stepped), j, lane,
-                                  cnt[wib], wsum[wib]);
+      pend &= ~shared_meet(src, A.T + ((rowbase[i + 1] + j) << tbits), tbits, stepped, x,
+                           pend, sg, j, cnt[wib], wsum[wib]);
       if (stepped) {
         next_mask((int64_t)(i + 1) * J + j);
         if (!pend) {
@@ -575,7 +560,7 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(0xffffffffu, st, off);
     warp_steps += st;
     __syncwarp();
-    if (lane < k && !((w_excl[wib] >> lane) & 1u)) {
+    if (lane < A.k && !((w_excl[wib] >> lane) & 1u)) {
       const ShSrc &S = src[lane];
       const unsigned long long W = wsum[wib][lane];
       S.scores[u] = (double)W * 2.3283064365386963e-10 / S.z;
@@ -667,30 +652,32 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // The shared-walk kernel: a persistent grid of as many 256-thread blocks as
 // fit at once (ctr[0]: the target counter, cleared here; ctr[1]: the steps).
-static void launch_shared(int layout, bool coop, cudaStream_t st, const BatchArgs &A,
+// The first walk index of source table t whose length is at least i (walks
+// are in stratum order): pairs below it cannot reach step i.
+static int32_t first_reaching(const QueryTab &t, int i) {
+  return i <= t.L ? t.P[i] : t.N_tot;
+}
+
+static void launch_shared(int layout, cudaStream_t st, const BatchArgs &A,
                           const int32_t *act, int32_t n_act, int32_t j0,
                           unsigned long long *ctr, int dev) {
-  static int per_sm[3][2][64] = {};
-  auto grid = [&](const void *f, int l, int c) {
-    int b = (dev >= 0 && dev < 64) ? per_sm[l][c][dev] : 0;
+  static int per_sm[3][64] = {};
+  auto grid = [&](const void *f, int l) {
+    int b = (dev >= 0 && dev < 64) ? per_sm[l][dev] : 0;
     if (!b) {
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, 0) != cudaSuccess || b < 1)
         b = 1;
-      if (dev >= 0 && dev < 64) per_sm[l][c][dev] = b;
+      if (dev >= 0 && dev < 64) per_sm[l][dev] = b;
     }
     return sm_count(dev) * b;
   };
-#define SRK_SH_LAUNCH(L, C)                                                           \
-  kb_shared_walks<L, C><<<grid((const void *)kb_shared_walks<L, C>, L, C), 256, 0, st>>>( \
+#define SRK_SH_LAUNCH(L)                                                         \
+  kb_shared_walks<L><<<grid((const void *)kb_shared_walks<L>, L), 256, 0, st>>>( \
       A, act, n_act, j0, ctr)
   cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st);
-  if (layout == kWide) {
-    if (coop) SRK_SH_LAUNCH(kWide, true); else SRK_SH_LAUNCH(kWide, false);
-  } else if (layout == kCsr) {
-    if (coop) SRK_SH_LAUNCH(kCsr, true); else SRK_SH_LAUNCH(kCsr, false);
-  } else {
-    if (coop) SRK_SH_LAUNCH(kNarrow, true); else SRK_SH_LAUNCH(kNarrow, false);
-  }
+  if (layout == kWide) SRK_SH_LAUNCH(kWide);
+  else if (layout == kCsr) SRK_SH_LAUNCH(kCsr);
+  else SRK_SH_LAUNCH(kNarrow);
 #undef SRK_SH_LAUNCH
 }
 
@@ -799,23 +786,34 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     size_t need = 0;
     int32_t i1 = i0;
     std::vector<size_t> ws_off;
-    int64_t sh_L = 1, sh_N = 0;  // shared walks: the records' extent so far
+    int64_t sh_L = 1, sh_N = 0;  // shared walks: the tables' extent so far
+    std::vector<int32_t> pmin((size_t)SRK_MAX_LEN + 2, INT32_MAX);
     while (i1 < k && !(shared && i1 - i0 >= 32)) {
-      if (shared) {  // the records are indexed with 32 bits
-        const int64_t L1 = std::max<int64_t>(sh_L, std::max(tabs[(size_t)i1].L, 1));
-        const int64_t N1 = std::max<int64_t>(sh_N, tabs[(size_t)i1].N_tot);
-        if (i1 > i0 && L1 * N1 * (i1 - i0 + 1) >= ((int64_t)1 << 31)) break;
-        sh_L = L1;
-        sh_N = N1;
+      // shared walks: the batch's mask rows and meeting tables with this source
+      int64_t L1 = sh_L, N1 = sh_N;
+      size_t sb = 0;
+      if (shared) {
+        const QueryTab &t = tabs[(size_t)i1];
+        L1 = std::max<int64_t>(sh_L, std::max(t.L, 1));
+        N1 = std::max<int64_t>(sh_N, t.N_tot);
+        int tb = 1;
+        while ((1 << tb) < 2 * (i1 - i0 + 1)) ++tb;
+        size_t tables = 0;
+        for (int i = 1; i <= L1; ++i)
+          tables += (size_t)(N1 - std::min<int64_t>(pmin[(size_t)i], first_reaching(t, i)));
+        sb = 16 * (size_t)(L1 + 1) * (size_t)N1 + ((8 * tables) << tb);
       }
       Workspace w;
       const QueryTab &t1 = tabs[(size_t)i1];
       const size_t b = align256(plan(t1, &w, nullptr)) +
                        (d_scores ? 0 : align256(8 * n)) + (d_counts ? 0 : align256(4 * n)) +
-                       (shared ? align256(4 * (size_t)std::max(t1.L, 1) * t1.N_tot) +
-                                     align256(8 * (size_t)t1.N_tot)
-                               : 0);  // (an upper bound of the source's share of the records)
-      if (i1 > i0 && need + b > budget) break;
+                       (shared ? align256(8 * (size_t)t1.N_tot) : 0);
+      if (i1 > i0 && need + b + sb > budget) break;
+      sh_L = L1;
+      sh_N = N1;
+      if (shared)
+        for (int i = 1; i <= SRK_MAX_LEN; ++i)
+          pmin[(size_t)i] = std::min(pmin[(size_t)i], first_reaching(tabs[(size_t)i1], i));
       ws_off.push_back(need);
       need += b;
       ++i1;
@@ -829,22 +827,27 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       Jmax = std::max(Jmax, t.N_tot);
       j0 = std::min(j0, t.L >= 1 ? t.P[1] : t.N_tot);  // below, every pair has length 0
     }
-    // shared walks: the warp-cooperative meeting test pays off when a pair is
-    // pending for several sources at once (an average of 4 or more at the
-    // first step, counting a source's pairs as pending up to its N_tot)
-    double pend_avg = 0.0;
-    for (int32_t b = i0; b < i1; ++b) pend_avg += (double)tabs[(size_t)b].N_tot / (double)Jmax;
-    const bool coop = pend_avg >= 4.0;
+    // shared walks: meeting tables of 2^tbits >= 2 kb slots, one per (step i,
+    // pair j >= pmin[i]), in rows by step: rowbase[i] + j is the table's index
+    int tbits = 1;
+    while ((1 << tbits) < 2 * kb) ++tbits;
+    std::vector<int64_t> rowbase((size_t)std::max(Lmax, 1) + 1, 0);
+    int64_t n_tables = 0;
+    for (int i = 1; i <= std::max(Lmax, 1); ++i) {
+      const int64_t pm = std::min<int64_t>(pmin[(size_t)i], Jmax);
+      rowbase[(size_t)i] = n_tables - pm;
+      n_tables += Jmax - pm;
+    }
     // shared walks: the step masks and signatures, Lmax + 1 rows of Jmax
-    // pairs of words, and the
-    // records, Lmax x Jmax x kb words
+    // 16-byte cells, the table rows and the tables
     const size_t m_bytes = shared ? 16 * (size_t)(Lmax + 1) * (size_t)Jmax : 0;
-    const size_t h_bytes = shared ? 4 * (size_t)std::max(Lmax, 1) * (size_t)Jmax * kb : 0;
+    const size_t r_bytes = shared ? sizeof(int64_t) * rowbase.size() : 0;
+    const size_t h_bytes = shared ? (8 * (size_t)n_tables) << tbits : 0;
     const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
                         align256(sizeof(int64_t) * (kb + 1)) +
                         align256(sizeof(int32_t) * (kb + 1)) +
                         align256(sizeof(unsigned long long) * (kb + 2)) + align256(m_bytes) +
-                        align256(h_bytes);
+                        align256(r_bytes) + align256(h_bytes);
     char *base = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&base, head + need, mp, st);
     if (e != cudaSuccess) { rc = cuda_fail(e, "batch workspace allocation"); break; }
@@ -855,7 +858,8 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     unsigned long long *d_ctr = (unsigned long long *)((char *)d_act_src +
                                                          align256(sizeof(int32_t) * (kb + 1)));
     uint4 *d_M = (uint4 *)((char *)d_ctr + align256(sizeof(unsigned long long) * (kb + 2)));
-    int32_t *d_H = (int32_t *)((char *)d_M + align256(m_bytes));
+    int64_t *d_rowbase = (int64_t *)((char *)d_M + align256(m_bytes));
+    uint2 *d_T = (uint2 *)((char *)d_rowbase + align256(r_bytes));
     // d_ctr[0] = item counter, d_ctr[1 + i] = steps of source i; n_act_src in d_act_src[kb]
     char *ws_base = base + head;
     std::vector<BatchSrc> hsrc((size_t)kb);
@@ -892,7 +896,9 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
         (e = cudaMemcpyAsync(d_src, hsrc.data(), sizeof(BatchSrc) * kb,
                              cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_off, hoff.data(), sizeof(int64_t) * (kb + 1),
-                             cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (shared && (e = cudaMemcpyAsync(d_rowbase, rowbase.data(), r_bytes,
+                                        cudaMemcpyHostToDevice, st)) != cudaSuccess)) {
       rc = cuda_fail(e, "batch descriptors");
       cudaFreeAsync(base, st);
       break;
@@ -911,7 +917,10 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     A.key1 = (uint32_t)(seed >> 32);
     A.shared_key = walk_key(seed, kSharedWalkKey);
     A.M = d_M;
-    A.H = d_H;
+    A.T = d_T;
+    A.rowbase = d_rowbase;
+    A.tbits = tbits;
+    A.Lmax = Lmax;
     A.Jmax = Jmax;
     const int gw = (int)std::max<int64_t>(1, std::min<int64_t>((A.total_walks + 255) / 256,
                                                                 (int64_t)sms * 8));
@@ -932,6 +941,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
       kb_pairs<<<gw, 256, 0, s2>>>(A);
       if (shared) {
         cudaMemsetAsync(d_M, 0, m_bytes, s2);
+        cudaMemsetAsync(d_T, 0, h_bytes, s2);
         kb_hitj<<<gw, 256, 0, s2>>>(A);
       } else {
         kb_rows<<<1, 256, 0, s2>>>(A, d_act_src, d_act_src + kb);
@@ -983,7 +993,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     auto enqueue_all = [&](cudaStream_t s2) {
       enqueue_source_side(s2);
       if (shared)
-        launch_shared(g->layout, coop, s2, A, g->act, g->n_act, j0, d_ctr, dev);
+        launch_shared(g->layout, s2, A, g->act, g->n_act, j0, d_ctr, dev);
       else
         launch_targets(g->layout, shape, sms, s2, A, g->act, g->n_act, d_act_src, d_act_src + kb,
                        d_ctr, INT64_MAX, Lmax);
