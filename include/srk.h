@@ -91,7 +91,7 @@ extern "C" {
                                   Each (s, u) estimate keeps its law; estimates
                                   of different sources share target walks.
                                   srk_multi_source then walks each target once
-                                  for all sources of a batch (up to 32 at a
+                                  for all sources of a batch (up to 64 at a
                                   time); its results equal those of
                                   srk_single_source with this flag */
 

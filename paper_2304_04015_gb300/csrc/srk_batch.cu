@@ -51,16 +51,16 @@ struct BatchArgs {
   int32_t pos_bits;
   uint32_t key0, key1;
   uint32_t shared_key;  // walk key of the shared target walks
-  uint4 *M;       // shared walks: M[(i-1) Jmax + j].x bit b = pair j of batch source
-                  // b may still meet at step i (cap_b(j) >= i); (.z, .w) = the
+  uint4 *M;       // shared walks: M[(i-1) Jmax + j] (.x, .y) bit b = pair j of batch
+                  // source b may still meet at step i (cap_b(j) >= i); (.z, .w) = the
                   // 64-bit signature of those sources' nodes at step i (bit
                   // node_hash(node) per node); Lmax + 1 rows
-  uint2 *T;       // shared walks: the meeting tables, one per (step i, pair j) with
+  uint4 *T;       // shared walks: the meeting tables, one per (step i, pair j) with
                   // j >= Pmin_i (below, no pair of the batch reaches step i) at
                   // T + ((rowbase[i] + j) << tbits): 2^tbits slots {node + 1,
-                  // the sources b with cap_b(j) >= i whose walk sigma_b(j) is at
-                  // that node at step i}, empty slots {0, 0}, linear probing from
-                  // slot_of(node)
+                  // (.y, .z) the sources b with cap_b(j) >= i whose walk
+                  // sigma_b(j) is at that node at step i}, empty slots 0,
+                  // linear probing from slot_of(node)
   const int64_t *rowbase;  // shared walks: rowbase[i] = tables before step i - Pmin_i
   int32_t tbits;  // shared walks: log2 of the slots per table (>= 2 k)
   int32_t Jmax;   // shared walks: the largest N_tot of the batch
@@ -337,7 +337,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
 // srk_single_source with the same flag decides it.  Those nodes of all the
 // batch's sources sit in one small hash table per (step, pair), so a walk
 // tests every pending source with one lookup of its own node (one sector,
-// rarely two).  Batches hold at most 32 sources (one mask bit each).
+// rarely two).  Batches hold at most 64 sources (one mask bit each).
 
 // One of 64 bits for a node: the signature of a (step, pair) record has the
 // bits of its nodes, so a walk whose node's bit is clear meets no source there.
@@ -368,21 +368,22 @@ __global__ void kb_hitj(const __grid_constant__ BatchArgs A) {
     S_.wj[j] = cap >= 1 ? __double2ull_rn(S_.tab->a[l1] * S_.tab->a[l2] * 4294967296.0) : 0ull;
     const int Ls = S_.L > 0 ? S_.L : 1;
     const int32_t *sp = S_.w.spos + (int64_t)w * Ls;
-    const uint32_t bit = 1u << i_;
+    const uint32_t bit = 1u << (i_ & 31);  // in word .x (sources 0-31) or .y (32-63)
+    const bool high = i_ >= 32;
     const uint32_t smask = (1u << A.tbits) - 1u;
     for (int q = 1; q <= cap; ++q) {
       const int32_t node = sp[q - 1];
       uint4 *cell = &A.M[(int64_t)(q - 1) * A.Jmax + j];
       const uint32_t h = node_hash(node);
-      atomicOr(&cell->x, bit);
+      atomicOr(high ? &cell->y : &cell->x, bit);
       atomicOr(h < 32 ? &cell->z : &cell->w, 1u << (h & 31));
-      uint2 *tab = A.T + ((A.rowbase[q] + j) << A.tbits);
+      uint4 *tab = A.T + ((A.rowbase[q] + j) << A.tbits);
       const uint32_t key = (uint32_t)node + 1u;
       uint32_t sl = slot_of(node, A.tbits);
       for (uint32_t probe = 0; probe <= smask; ++probe, sl = (sl + 1u) & smask) {
         const uint32_t prev = atomicCAS(&tab[sl].x, 0u, key);
         if (prev == 0u || prev == key) {
-          atomicOr(&tab[sl].y, bit);
+          atomicOr(high ? &tab[sl].z : &tab[sl].y, bit);
           break;
         }
       }
@@ -404,24 +405,23 @@ struct ShSrc {
 // pending sources among the slot's are those that meet here.  Their counts
 // and weight sums go to the warp's shared words cnt[b], wsum[b] (atomics:
 // lanes of a warp can meet the same source at once).  Returns them.
-__device__ __forceinline__ uint32_t shared_meet(const ShSrc *src, const uint2 *tab, int tbits,
-                                                bool stepped, int32_t x, uint32_t pend,
-                                                uint2 sig, int32_t j,
-                                                uint32_t *cnt, unsigned long long *wsum) {
-  uint32_t hits = 0u;
-  if (stepped && pend != 0u && sig_has(sig, x)) {
+__device__ __forceinline__ unsigned long long shared_meet(
+    const ShSrc *src, const uint4 *tab, int tbits, bool stepped, int32_t x,
+    unsigned long long pend, uint2 sig, int32_t j, uint32_t *cnt, unsigned long long *wsum) {
+  unsigned long long hits = 0ull;
+  if (stepped && pend != 0ull && sig_has(sig, x)) {
     const uint32_t smask = (1u << tbits) - 1u, key = (uint32_t)x + 1u;
     uint32_t sl = slot_of(x, tbits);
     for (uint32_t probe = 0; probe <= smask; ++probe, sl = (sl + 1u) & smask) {
-      const uint2 e = tab[sl];
+      const uint4 e = tab[sl];
       if (e.x == key) {
-        hits = e.y & pend;
+        hits = (((unsigned long long)e.z << 32) | e.y) & pend;
         break;
       }
       if (e.x == 0u) break;
     }
-    for (uint32_t m = hits; m; m &= m - 1) {
-      const int b = __ffs(m) - 1;
+    for (unsigned long long m = hits; m; m &= m - 1) {
+      const int b = __ffsll((long long)m) - 1;
       atomicAdd(&cnt[b], 1u);
       atomicAdd(&wsum[b], src[b].wj[j]);
     }
@@ -444,12 +444,13 @@ template <int kLayout>
 __global__ void __launch_bounds__(256, 6)
 kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__ act,
                 int32_t n_act, int32_t j0, unsigned long long *__restrict__ ctr) {
-  __shared__ ShSrc src[32];
-  __shared__ uint32_t cnt[8][32];
-  __shared__ unsigned long long wsum[8][32];
+  __shared__ ShSrc src[64];
+  __shared__ uint32_t cnt[8][64];
+  __shared__ unsigned long long wsum[8][64];
   // per warp: the sources whose own row the target is, and the target's list
   // (read at refills only, so they hold no registers across the walk)
-  __shared__ uint32_t w_excl[8], w_deg[8];
+  __shared__ unsigned long long w_excl[8];
+  __shared__ uint32_t w_deg[8];
   __shared__ int32_t w_base[8];
   __shared__ long long rowbase[SRK_MAX_LEN + 2];  // meeting-table rows (A.rowbase)
   for (int i = threadIdx.x; i <= SRK_MAX_LEN + 1; i += blockDim.x)
@@ -473,9 +474,15 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     if (q >= n_act) break;
     const uint32_t u = (uint32_t)act[q];
     // sources whose own row this target is
-    const uint32_t excl = __ballot_sync(0xffffffffu, lane < A.k && src[lane].s == (int32_t)u);
-    cnt[wib][lane] = 0u;            // meetings of source `lane` at this target
-    wsum[wib][lane] = 0ull;         // and their weight sum
+    const unsigned long long excl =
+        __ballot_sync(0xffffffffu, lane < A.k && src[lane].s == (int32_t)u) |
+        ((unsigned long long)__ballot_sync(0xffffffffu, lane + 32 < A.k &&
+                                                       src[lane + 32].s == (int32_t)u)
+         << 32);
+    cnt[wib][lane] = 0u;            // meetings of sources `lane`, `lane` + 32 at this target
+    cnt[wib][lane + 32] = 0u;
+    wsum[wib][lane] = 0ull;         // and their weight sums
+    wsum[wib][lane + 32] = 0ull;
     if (lane == 0) {
       uint32_t deg_u = 0;
       w_base[wib] = node_start(G, A.row_ptr, (int32_t)u, deg_u);
@@ -486,12 +493,13 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     uint32_t st = 0;
     int32_t next = j0, j = 0, i = 1, b = 0;
     bool live = false;
-    uint32_t deg = 0, pend = 0;
+    uint32_t deg = 0;
+    unsigned long long pend = 0ull;
     uint2 sg = make_uint2(0u, 0u);  // the signature of the next test
     // pend &= the mask of row `row`; sg = its signature
     auto next_mask = [&](int64_t row) {
       const uint4 mn = M[row];
-      pend &= mn.x;
+      pend &= ((unsigned long long)mn.y << 32) | mn.x;
       sg = make_uint2(mn.z, mn.w);
     };
     for (;;) {
@@ -501,9 +509,9 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
           j = next + __popc(idle & lanes_below_mask());
           if (j < J) {
             const uint4 m1 = M[j];
-            pend = m1.x & ~w_excl[wib];
+            pend = (((unsigned long long)m1.y << 32) | m1.x) & ~w_excl[wib];
             sg = make_uint2(m1.z, m1.w);
-            live = pend != 0u;
+            live = pend != 0ull;
             i = 1;
             b = w_base[wib];
             deg = w_deg[wib];
@@ -560,11 +568,12 @@ kb_shared_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
     for (int off = 16; off > 0; off >>= 1) st += __shfl_xor_sync(0xffffffffu, st, off);
     warp_steps += st;
     __syncwarp();
-    if (lane < A.k && !((w_excl[wib] >> lane) & 1u)) {
-      const ShSrc &S = src[lane];
-      const unsigned long long W = wsum[wib][lane];
+    for (int bb = lane; bb < A.k; bb += 32) {
+      if ((w_excl[wib] >> bb) & 1ull) continue;
+      const ShSrc &S = src[bb];
+      const unsigned long long W = wsum[wib][bb];
       S.scores[u] = (double)W * 2.3283064365386963e-10 / S.z;
-      if (S.counts) S.counts[u] = cnt[wib][lane];
+      if (S.counts) S.counts[u] = cnt[wib][bb];
     }
     __syncwarp();
   }
@@ -788,7 +797,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     std::vector<size_t> ws_off;
     int64_t sh_L = 1, sh_N = 0;  // shared walks: the tables' extent so far
     std::vector<int32_t> pmin((size_t)SRK_MAX_LEN + 2, INT32_MAX);
-    while (i1 < k && !(shared && i1 - i0 >= 32)) {
+    while (i1 < k && !(shared && i1 - i0 >= 64)) {
       // shared walks: the batch's mask rows and meeting tables with this source
       int64_t L1 = sh_L, N1 = sh_N;
       size_t sb = 0;
@@ -801,7 +810,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
         size_t tables = 0;
         for (int i = 1; i <= L1; ++i)
           tables += (size_t)(N1 - std::min<int64_t>(pmin[(size_t)i], first_reaching(t, i)));
-        sb = 16 * (size_t)(L1 + 1) * (size_t)N1 + ((8 * tables) << tb);
+        sb = 16 * (size_t)(L1 + 1) * (size_t)N1 + ((16 * tables) << tb);
       }
       Workspace w;
       const QueryTab &t1 = tabs[(size_t)i1];
@@ -842,7 +851,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
     // 16-byte cells, the table rows and the tables
     const size_t m_bytes = shared ? 16 * (size_t)(Lmax + 1) * (size_t)Jmax : 0;
     const size_t r_bytes = shared ? sizeof(int64_t) * rowbase.size() : 0;
-    const size_t h_bytes = shared ? (8 * (size_t)n_tables) << tbits : 0;
+    const size_t h_bytes = shared ? (16 * (size_t)n_tables) << tbits : 0;
     const size_t head = align256(sizeof(BatchSrc) * kb) + align256(sizeof(QueryTab) * kb) +
                         align256(sizeof(int64_t) * (kb + 1)) +
                         align256(sizeof(int32_t) * (kb + 1)) +
@@ -859,7 +868,7 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
                                                          align256(sizeof(int32_t) * (kb + 1)));
     uint4 *d_M = (uint4 *)((char *)d_ctr + align256(sizeof(unsigned long long) * (kb + 2)));
     int64_t *d_rowbase = (int64_t *)((char *)d_M + align256(m_bytes));
-    uint2 *d_T = (uint2 *)((char *)d_rowbase + align256(r_bytes));
+    uint4 *d_T = (uint4 *)((char *)d_rowbase + align256(r_bytes));
     // d_ctr[0] = item counter, d_ctr[1 + i] = steps of source i; n_act_src in d_act_src[kb]
     char *ws_base = base + head;
     std::vector<BatchSrc> hsrc((size_t)kb);

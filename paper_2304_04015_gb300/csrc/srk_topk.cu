@@ -272,7 +272,7 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
   // chunk of sources whose dense rows fit the scratch budget
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  size_t budget = std::max<size_t>((size_t)64 << 20, std::min<size_t>((size_t)4 << 30, free_b / 8));
+  size_t budget = std::max<size_t>((size_t)64 << 20, std::min<size_t>((size_t)16 << 30, free_b / 8));
   if (const char *env = getenv("SRK_TOPK_ROWS_BYTES")) {
     const unsigned long long v = strtoull(env, nullptr, 10);
     if (v > 0) budget = (size_t)v;

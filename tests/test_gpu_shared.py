@@ -5,7 +5,7 @@ draws every node's walks once.  srk_single_source with the flag must equal the
 oracle's shared mode bit for bit (counts, weight sums, step counts, scores);
 srk_multi_source with the flag walks each target once for all sources of a
 batch and must equal the single-source queries bit for bit (scores, counts),
-with or without graph capture, over several batches of up to 32 sources, with
+with or without graph capture, over several batches of up to 64 sources, with
 host or device outputs; at R-MAT 16 it is also checked against the oracle on
 sampled targets.
 """
@@ -85,25 +85,27 @@ def test_shared_batch_equals_single_queries(srk):
         g.close()
 
 
-def test_shared_batches_of_32_and_the_rest(srk, monkeypatch):
-    # 40 sources: a batch of 32 and one of 8; a small scratch budget splits
-    # them further; sources repeat and are targets of one another
+def test_shared_batches_of_64_and_the_rest(srk, monkeypatch):
+    # 70 sources: a batch of 64 (masks and tables span both 32-bit words) and
+    # one of 6; a small scratch budget splits them further; sources repeat
+    # and are targets of one another
     import torch
     dev = torch.device("cuda:0")
     rp, col = er_graph(300, 4.0, 3)
     n = rp.size - 1
     rng = np.random.default_rng(2)
-    sources = [int(x) for x in rng.integers(0, n, size=40)]
+    sources = [int(x) for x in rng.integers(0, n, size=70)]
     sources[5] = sources[4]
-    eps = [float(x) for x in rng.choice([0.2, 0.3, 0.5], size=40)]
+    sources[50] = sources[4]
+    eps = [float(x) for x in rng.choice([0.2, 0.3, 0.5], size=70)]
     g = srk.srk_graph_load(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev))
     try:
         ref_s, ref_c = _single_rows(srk, g, n, sources, eps, 4, dev, z_override=400.0)
         for budget in (None, "2000000"):
             if budget:
                 monkeypatch.setenv("SRK_BATCH_BYTES", budget)
-            out = torch.empty((40, n), dtype=torch.float64, device=dev)
-            cnt = torch.empty((40, n), dtype=torch.int32, device=dev)
+            out = torch.empty((70, n), dtype=torch.float64, device=dev)
+            cnt = torch.empty((70, n), dtype=torch.int32, device=dev)
             srk.srk_multi_source(g, sources, C, eps, 4, out, cnt, shared_walks=True,
                                  z_override=400.0)
             torch.cuda.synchronize()
