@@ -715,6 +715,37 @@ static cudaStream_t capture_stream(int dev) {
 
 using namespace srk;
 
+namespace srk {
+
+__global__ void k_source_degrees(const int32_t *__restrict__ row_ptr,
+                                 int32_t *__restrict__ v, int32_t k) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) v[i] = row_ptr[v[i] + 1] - row_ptr[v[i]];
+}
+
+int source_in_degrees(const srk_graph *g, const int32_t *sources, int32_t k, cudaStream_t st,
+                      std::vector<int32_t> *deg) {
+  deg->assign((size_t)k, 0);
+  if (k <= 0) return SRK_OK;
+  cudaMemPool_t mp = pool(g->device);
+  if (!mp) return fail(SRK_ECUDA, "cannot create the device memory pool");
+  int32_t *d = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync((void **)&d, sizeof(int32_t) * (size_t)k, mp, st);
+  if (e != cudaSuccess) return cuda_fail(e, "source degrees: allocation");
+  e = cudaMemcpyAsync(d, sources, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_source_degrees<<<(k + 255) / 256, 256, 0, st>>>(g->row_ptr, d, k);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(deg->data(), d, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SRK_OK : cuda_fail(e, "source degrees");
+}
+
+}  // namespace srk
+
 extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
                                 int32_t k, double c, const double *eps,
                                 uint64_t seed, const srk_opts *opt,
@@ -748,16 +779,23 @@ extern "C" int srk_multi_source(const srk_graph *g, const int32_t *sources,
   // depend on its batch, since its target walks do not depend on it.
   std::vector<int32_t> row_of((size_t)k);
   for (int32_t i = 0; i < k; ++i) row_of[(size_t)i] = i;
+  DeviceGuard guard(g->device);
   if (shared) {
+    // sources without in-neighbours go last: their pairs meet nowhere, so they
+    // would hold places in batches that share walks
+    std::vector<int32_t> deg;
+    const int rcd = source_in_degrees(g, sources, k, (cudaStream_t)cuda_stream, &deg);
+    if (rcd) return rcd;
     std::stable_sort(row_of.begin(), row_of.end(), [&](int32_t a, int32_t b) {
       const QueryTab &ta = tabs[(size_t)a], &tb = tabs[(size_t)b];
+      const bool za = deg[(size_t)a] == 0, zb = deg[(size_t)b] == 0;
+      if (za != zb) return zb;
       return ta.N_tot != tb.N_tot ? ta.N_tot < tb.N_tot : ta.L < tb.L;
     });
     std::vector<QueryTab> sorted((size_t)k);
     for (int32_t p = 0; p < k; ++p) sorted[(size_t)p] = tabs[(size_t)row_of[(size_t)p]];
     tabs.swap(sorted);
   }
-  DeviceGuard guard(g->device);
   const int dev = g->device;
   const int sms = sm_count(dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;

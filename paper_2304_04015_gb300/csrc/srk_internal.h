@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "srk.h"
 
 struct srk_graph {
@@ -162,6 +164,11 @@ int target_range(const srk_graph *g, const srk_opts *opt, int32_t *b, int32_t *e
 __global__ void k_scan(const int32_t *__restrict__ cnt, int32_t *__restrict__ off,
                        int32_t N);
 
+
+// In-degrees of k sources (ids already checked against n), read from the
+// device CSR on stream st (synchronises st).  SRK_OK or an error code.
+int source_in_degrees(const srk_graph *g, const int32_t *sources, int32_t k, cudaStream_t st,
+                      std::vector<int32_t> *deg);
 
 // Releases the graph's linear topology, if built (srk_linear.cu).
 void free_lin_topo(srk_graph *g);

@@ -277,7 +277,8 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
     const unsigned long long v = strtoull(env, nullptr, 10);
     if (v > 0) budget = (size_t)v;
   }
-  const int32_t R = (int32_t)std::max<int64_t>(1, std::min<int64_t>(k, (int64_t)(budget / (8 * (size_t)n))));
+  int32_t R = (int32_t)std::max<int64_t>(1, std::min<int64_t>(k, (int64_t)(budget / (8 * (size_t)n))));
+  if (R >= 64 && R < k) R -= R % 64;  // whole batches of shared target walks
   const int32_t n_chunks = (int32_t)((n + kChunk - 1) / kChunk);
   int P = 1;
   while (P < top) P <<= 1;
@@ -301,14 +302,25 @@ extern "C" int srk_multi_source_topk(const srk_graph *g, const int32_t *sources,
   int32_t *sid = (int32_t *)((char *)skey + b_key);
   int32_t *dsrc = (int32_t *)((char *)sid + b_id);
   int32_t *ddst = (int32_t *)((char *)dsrc + b_src);
-  // the order the sources run in: as given, or grouped by eps (descending,
-  // so by walk budget) when they share target walks, so that a chunk's
-  // batches share as many pairs as possible
+  // the order the sources run in: as given, or, when they share target walks,
+  // the sources with in-neighbours grouped by eps (descending, so by walk
+  // budget) and the others last, so that a chunk's batches share as many
+  // pairs as possible
   std::vector<int32_t> order((size_t)k);
   for (int32_t i = 0; i < k; ++i) order[(size_t)i] = i;
-  if (opt && (opt->flags & SRK_OPT_SHARED_WALKS))
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return eps[a] > eps[b]; });
+  if (opt && (opt->flags & SRK_OPT_SHARED_WALKS)) {
+    for (int32_t i = 0; i < k; ++i)
+      if (sources[i] < 0 || sources[i] >= g->n)
+        return fail(SRK_EINVAL, "source %d (index %d) outside [0, %d)", sources[i], i, g->n);
+    std::vector<int32_t> deg;
+    const int rcd = source_in_degrees(g, sources, k, st, &deg);
+    if (rcd) return rcd;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      const bool za = deg[(size_t)a] == 0, zb = deg[(size_t)b] == 0;
+      if (za != zb) return zb;
+      return eps[a] > eps[b];
+    });
+  }
   std::vector<int32_t> src_o((size_t)k);
   std::vector<double> eps_o((size_t)k);
   for (int32_t i = 0; i < k; ++i) {
