@@ -247,17 +247,32 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes per target-walk step of the target-walk kernel, from the
-    committed ncu summary, if it was taken on the current kernel sources."""
+def recorded_profile():
+    """The committed ncu record of the target-walk kernel, if it was taken on
+    the current kernel sources, else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_target_walks_rmat20_traffic.json")) as f:
             rec = json.load(f)
-        if rec.get("kernel_sources_sha256") != kernel_source_sha256():
-            return None
-        return float(rec["dram_bytes_per_launch"]) / float(rec["target_steps_of_launch"])
+        return rec if rec.get("kernel_sources_sha256") == kernel_source_sha256() else None
     except Exception:
         return None
+
+
+def recorded_traffic():
+    """DRAM bytes per target-walk step of the target-walk kernel, from the
+    committed ncu summary, if it was taken on the current kernel sources."""
+    rec = recorded_profile()
+    if rec is None:
+        return None
+    return float(rec["dram_bytes_per_launch"]) / float(rec["target_steps_of_launch"])
+
+
+def recorded_l2_sectors():
+    """L2 sectors requested by L1 per target-walk step (ncu, current sources)."""
+    rec = recorded_profile()
+    if rec is None or "l2_sectors_from_l1_of_launch" not in rec:
+        return None
+    return float(rec["l2_sectors_from_l1_of_launch"]) / float(rec["target_steps_of_launch"])
 
 
 def cpu_baseline(rp, col, sources, budget_s, **variant):
@@ -953,6 +968,16 @@ def main():
                                  "size of the adjacency (%d MB)" % (adj_b >> 20),
                     "unit_name": "target-walk step (one dependent scattered adjacency load)",
                     **common}
+        sps = recorded_l2_sectors()
+        if sps is not None:
+            # each probe load misses L1 and takes one L2 sector; a step of the
+            # kernel takes fewer (some of its loads hit L1)
+            roofline["l2_sectors"] = {
+                "per_step": sps, "achieved": target_steps_per_s * sps / 1e9,
+                "peak": l2_rate / 1e9, "unit": "Gsectors/s",
+                "frac": target_steps_per_s * sps / l2_rate,
+                "source": "L2 sectors requested by L1 per step from the recorded ncu "
+                          "capture of these kernel sources"}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": peak_hbm,
                     "unit": "GB/s", "frac": hbm_frac,
