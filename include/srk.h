@@ -240,7 +240,11 @@ int srk_single_source(const srk_graph *g, int32_t s, double c, double eps,
  * produce no work items; their scores are written directly.  The persistent
  * kernel's launch shape is picked per graph by timing the candidate shapes on
  * the first items of the first call (kept in the handle).  The call
- * synchronises the stream at the end of every batch.  opt->step_counts must
+ * synchronises the stream at the end of every batch.  With
+ * SRK_OPT_SHARED_WALKS the batches hold up to 64 sources, grouped by walk
+ * budget with the sources without in-neighbours last (the call first reads
+ * the sources' in-degrees from the device CSR, synchronising the stream);
+ * rows still land in the caller's order.  opt->step_counts must
  * be NULL, and target ranges and SRK_OPT_LITERAL_SHUFFLE are refused
  * (SRK_EINVAL); opt->stats, if set, receives totals over all sources.
  */
@@ -263,8 +267,11 @@ int srk_multi_source(const srk_graph *g, const int32_t *sources, int32_t k,
  *   nnz        : NULL or k int64 (device): targets with a nonzero score.
  * The scores are exactly those of srk_multi_source (same options, including
  * SRK_OPT_SHARED_WALKS).  Sources run in chunks whose dense rows fit a
- * scratch budget (an eighth of free device memory, at most 4 GiB, or the
- * byte count in SRK_TOPK_ROWS_BYTES); each chunk's rows are selected on the
+ * scratch budget (an eighth of free device memory, at most 16 GiB, or the
+ * byte count in SRK_TOPK_ROWS_BYTES; a multiple of 64 rows when 64 or more
+ * fit); with SRK_OPT_SHARED_WALKS the chunks take the sources with
+ * in-neighbours by eps, descending, and the others last (sources outside
+ * [0, n) are refused, SRK_EINVAL).  Each chunk's rows are selected on the
  * device by a radix select over the scores' bit patterns.  1 <= top <= 4096
  * (SRK_EINVAL otherwise); host output pointers are refused (SRK_EINVAL).
  */
