@@ -354,6 +354,7 @@ def run_batch(args, rank, world):
     all_eps = mixed_eps(4096, seed=3)
     third = 4096 // 3
     order = [g * third + i for i in range(third) for g in range(3)]
+    order += list(range(3 * third, 4096))  # the last group's extra source
     pick = order[:args.batch_sources]
     sources = [int(all_src[i]) for i in pick]
     eps = [float(all_eps[i]) for i in pick]
