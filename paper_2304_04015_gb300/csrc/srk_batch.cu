@@ -269,8 +269,7 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
   __shared__ PairSet ctx[kBlock / 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
-  int32_t *my_cnt = rows + (2 * wib) * row_words;
-  int32_t *my_R = my_cnt + row_words;
+  int2 *my_rc = reinterpret_cast<int2 *>(rows + (2 * wib) * row_words);
   const int64_t n_items = (int64_t)(*n_act_src_p) * n_act;
   const int64_t limit = item_limit < n_items ? item_limit : n_items;
   int cur = -1;
@@ -290,14 +289,11 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
       const BatchSrc &B = A.src[i];
       const Small sm = small_view(B.w.small);
       __syncwarp();
-      for (int x = lane; x <= B.L + 2; x += 32) {
-        my_cnt[x] = (x <= B.L + 1) ? sm.cnt[x] : 0;
-        my_R[x] = (x <= B.L + 1) ? sm.R[x] : 0;
-      }
+      for (int x = lane; x <= B.L + 2; x += 32)
+        my_rc[x] = make_int2((x <= B.L + 1) ? sm.R[x] : 0, (x + 1 <= B.L + 1) ? sm.cnt[x + 1] : 0);
       if (lane == 0) {
         PairSet &S = ctx[wib];
-        S.cnt = my_cnt;
-        S.R = my_R;
+        S.rc = my_rc;
         S.pair_j = B.w.pair_j;
         S.pair_w = B.w.pair_w;
         S.Hc = B.w.Hc;

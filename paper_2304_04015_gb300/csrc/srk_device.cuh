@@ -348,8 +348,8 @@ __device__ __forceinline__ int32_t resolve_sigma(int32_t j, const int32_t *kdraw
 
 // One source's pairs as the target walks see them.
 struct PairSet {
-  const int32_t *cnt;  // cnt[i] = pairs with cap >= i, cnt[L+1] = 0
-  const int32_t *R;    // hit-table row offsets
+  const int2 *rc;      // rc[i] = {R[i], cnt[i+1]}: hit-table row i's offset and the
+                       // pairs with cap >= i+1 (cnt[L+1] = cnt[L+2] = 0)
   const int32_t *pair_j;
   const unsigned long long *pair_w;
   const int32_t *Hc;
@@ -392,11 +392,12 @@ __device__ __forceinline__ void walk_target(const GA &G,
       auto e = step_entry(G, b, x0, deg, S.key, i, j, u);
       int32_t x = entry_pos(G, e);
       ++st;
-      if (x == S.Hc[S.R[i] + a]) {
+      const int2 r1 = S.rc[i];
+      if (x == S.Hc[r1.x + a]) {
         ++c;
         W += S.pair_w[a];
         live = false;
-      } else if (a >= S.cnt[i + 1]) {
+      } else if (a >= r1.y) {
         live = false;  // cap reached
       } else {
         b = entry_next(G, e, x, deg);
@@ -407,11 +408,12 @@ __device__ __forceinline__ void walk_target(const GA &G,
           e = step_entry(G, b, x1, deg, S.key, i + 1, j, u);
           x = entry_pos(G, e);
           ++st;
-          if (x == S.Hc[S.R[i + 1] + a]) {
+          const int2 r2 = S.rc[i + 1];
+          if (x == S.Hc[r2.x + a]) {
             ++c;
             W += S.pair_w[a];
             live = false;
-          } else if (a >= S.cnt[i + 2]) {
+          } else if (a >= r2.y) {
             live = false;
           } else {
             b = entry_next(G, e, x, deg);
@@ -555,11 +557,12 @@ __device__ __forceinline__ void walk_target_literal(
       auto e = step_entry(G, b, x0, deg, S.key, i, t, u);
       int32_t x = entry_pos(G, e);
       ++st;
-      if (x == S.Hc[S.R[i] + a]) {
+      const int2 r1 = S.rc[i];
+      if (x == S.Hc[r1.x + a]) {
         ++c;
         W += __double2ull_rn(aw[(int)S.pair_w[a]] * aw[l2] * 4294967296.0);
         live = false;
-      } else if (a >= S.cnt[i + 1] || i >= l2) {
+      } else if (a >= r1.y || i >= l2) {
         live = false;
       } else {
         b = entry_next(G, e, x, deg);
@@ -569,11 +572,12 @@ __device__ __forceinline__ void walk_target_literal(
           e = step_entry(G, b, x1, deg, S.key, i + 1, t, u);
           x = entry_pos(G, e);
           ++st;
-          if (x == S.Hc[S.R[i + 1] + a]) {
+          const int2 r2 = S.rc[i + 1];
+          if (x == S.Hc[r2.x + a]) {
             ++c;
             W += __double2ull_rn(aw[(int)S.pair_w[a]] * aw[l2] * 4294967296.0);
             live = false;
-          } else if (a >= S.cnt[i + 2] || i + 1 >= l2) {
+          } else if (a >= r2.y || i + 1 >= l2) {
             live = false;
           } else {
             b = entry_next(G, e, x, deg);

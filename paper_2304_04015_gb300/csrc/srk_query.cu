@@ -308,14 +308,13 @@ struct LiteralArgs {
 template <bool kLiteral, int kLayout>
 __global__ void __launch_bounds__(256, 8)
 k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ LiteralArgs X) {
-  __shared__ int32_t cnt[SRK_MAX_LEN + 3];
-  __shared__ int32_t R[SRK_MAX_LEN + 3];
+  __shared__ int2 rc[SRK_MAX_LEN + 3];  // {R[i], cnt[i+1]}, one load per step
   __shared__ int32_t Psh[kLiteral ? SRK_MAX_LEN + 2 : 1];
   {
     const Small sm = small_view(const_cast<int32_t *>(A.small_base));
     for (int i = threadIdx.x; i <= A.L + 2; i += blockDim.x) {
-      cnt[i] = (i <= A.L + 1) ? sm.cnt[i] : 0;  // cnt[L+1] = cnt[L+2] = 0
-      R[i] = (i <= A.L + 1) ? sm.R[i] : 0;
+      rc[i] = make_int2((i <= A.L + 1) ? sm.R[i] : 0,
+                        (i + 1 <= A.L + 1) ? sm.cnt[i + 1] : 0);  // cnt[L+1] = cnt[L+2] = 0
       if (kLiteral && i <= A.L + 1) Psh[i] = X.P[i];
     }
   }
@@ -324,12 +323,11 @@ k_target_walks(const __grid_constant__ TargetArgs A, const __grid_constant__ Lit
   const uint32_t lanes_below = (1u << lane) - 1u;
   const auto G = adj_view<kLayout>(A.adj, A.npos, A.pos_bits, A.row_ptr, A.col);
   PairSet S;
-  S.cnt = cnt;
-  S.R = R;
+  S.rc = rc;
   S.pair_j = A.pair_j;
   S.pair_w = A.pair_w;
   S.Hc = A.Hc;
-  S.n_pairs = cnt[1];
+  S.n_pairs = rc[0].y;  // cnt[1]
   S.key = A.walk_key;
   FeistelShape fs;
   if constexpr (kLiteral)
