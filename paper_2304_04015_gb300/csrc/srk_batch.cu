@@ -13,7 +13,9 @@
 // neither do targets without in-neighbours.  A batch's launches are captured
 // in a CUDA graph and launched as one.  The persistent kernel's launch shape
 // (block size x blocks per SM) is chosen per graph by timing the candidates
-// on the first items of the first batch (autotuner).
+// on the first items of the first batch (autotuner).  With shared target walks
+// (SRK_OPT_SHARED_WALKS) the batches hold up to 64 sources and the target
+// walks run once for all of them (kb_shared_walks, below).
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -335,8 +337,9 @@ kb_target_walks(const __grid_constant__ BatchArgs A, const int32_t *__restrict__
 // tests every pending source with one lookup of its own node (one sector,
 // rarely two).  Batches hold at most 64 sources (one mask bit each).
 
-// One of 64 bits for a node: the signature of a (step, pair) record has the
-// bits of its nodes, so a walk whose node's bit is clear meets no source there.
+// One of 64 bits for a node: the signature of a (step, pair) has the bits of
+// the pending sources' nodes there, so a walk whose node's bit is clear
+// meets no source there.
 __device__ __forceinline__ uint32_t node_hash(int32_t x) {
   return ((uint32_t)x * 0x9E3779B9u) >> 26;
 }
