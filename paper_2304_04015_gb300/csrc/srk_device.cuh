@@ -78,7 +78,8 @@ __device__ __forceinline__ uint32_t draw_index(uint32_t hi, uint32_t lo,
 }
 
 // Walk steps.  Step i of walk replica r from node v, under the query's walk
-// key k (walk_key): block ((i-1)>>1) << 24 | r, v) of Philox2x32-10 serves
+// key k (walk_key): the Philox2x32-10 block of counter
+// (((i-1)>>1) << 24 | r, v) serves
 // the odd step i = 2t+1 (word x0) and the even step 2t+2 (word x1)
 // (r < 2^24, t < 2^7, v < 2^31: the top bits of both counter words stay
 // clear).  The in-neighbour index below d is Lemire's bounded draw ("Fast
@@ -103,8 +104,8 @@ static __device__ __noinline__ uint32_t step_index_redraw(uint32_t k, int i, uin
   return draw_index(y0, y1, d);
 }
 
-// The lane's position among the warp's lanes below it (a mask), read from the
-// special register rather than kept live across the walk loop.
+// The mask of the warp's lanes below this one, read from the special
+// register rather than kept live across the walk loop.
 __device__ __forceinline__ uint32_t lanes_below_mask() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
