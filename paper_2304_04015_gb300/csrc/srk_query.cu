@@ -28,7 +28,8 @@ namespace srk {
 // Walk r of the source has length l = stratum(r).  Step i >= 1 moves to
 // I(x)[k], k the bounded draw below |I(x)| from word (i-1)&1 of the
 // Philox2x32-10 block (((i-1)>>1) << 24 | r, s) under the source's walk key
-// (step_entry); it stops early at a node with no in-neighbours.  Walks run on the graph's adjacency layout (a packed copy
+// (step_entry); it stops early at a node with no in-neighbours.  Walks run
+// on the graph's adjacency layout (a packed copy
 // in which nodes are identified by their position, or the CSR itself).  The
 // same thread computes Fisher-Yates draw t = r, k_t = floor(R * (t+1) / 2^64)
 // with R from counter (t>>1, ~0, ~0, s).
